@@ -1,0 +1,204 @@
+/*
+ * libdie -- C ABI of the GB300 TE domain-integral-equation solver.
+ *
+ * Zouros & Budko, "Transverse electric scattering on inhomogeneous objects:
+ * spectrum of integral operator and preconditioning" (arXiv 1104.4263).
+ *
+ * The operator.  On an n1 x n2 grid of square cells of side h (cell centres
+ * x_i = (i + 1/2) h - n h / 2), with relative permittivity eps_r(x), contrast
+ * chi = eps_r - 1 (Eq. (2.11), eps_b = 1) and unknowns u = (E1, E2), the
+ * midpoint-collocation system of Section 4, Eqs. (4.1)-(4.5), restricted to the
+ * electric unknowns (no magnetic contrast, so Eqs. (4.6)-(4.11) drop out) is
+ *     A u = b,   A = I - G X(chi),
+ *     (G w)_l(x_n) = sum_m sum_q G_lq(x_n - x_m) w_q(x_m),
+ * with G_lq from Eqs. (4.3)-(4.5) (Hankel functions of k_b |x_n - x_m|; the
+ * diagonal from the equal-area disc of Eq. (4.4)).  The regularised operator of
+ * Eq. (3.19) and Section 5 is A_R A with A_R = A(chi'), chi' = 1/eps_r - 1
+ * (Eq. (3.18)).  G is block-Toeplitz, so every product runs as a zero-padded 2-D
+ * FFT convolution (Sections 1 and 5).
+ *
+ * Vector layout.  A field vector is 2 * n1 * n2 interleaved complex numbers in
+ * the order [component][x2][x1] (x1 fastest): E1 plane, then E2 plane.
+ * Complex128 = two doubles (re, im); complex64 = two floats.
+ *
+ * Conventions for every call:
+ *  - device pointers are CUDA global-memory pointers on the current device; the
+ *    caller owns them and must keep them alive until the stream reaches the call;
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream); every call is
+ *    stream-ordered on it; calls that report values to the host synchronise it;
+ *  - handles are not thread-safe: one host thread at a time per handle;
+ *  - no call aborts or traps: failures return a die_status; after DIE_ECUDA the
+ *    handle should be destroyed.
+ */
+#ifndef LIBDIE_DIE_H
+#define LIBDIE_DIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIE_ABI_VERSION 1
+
+typedef enum die_status {
+    DIE_OK = 0,
+    DIE_EINVAL = 1,        /* bad argument (sizes, NULL pointer, unsupported option)          */
+    DIE_ENOMEM = 2,        /* device or host allocation failed                                 */
+    DIE_ECUDA = 3,         /* a CUDA runtime call failed                                       */
+    DIE_ESINGULAR = 4,     /* eps_r == 0 somewhere (existence condition, Eq. (3.17)), or T singular */
+    DIE_ENOCONV = 5,       /* GMRES / eigensolver stopped at max_iters without reaching tol    */
+    DIE_EBREAKDOWN = 6,    /* Arnoldi breakdown with a singular least-squares problem          */
+    DIE_ENAN = 7,          /* NaN or Inf met in a residual or norm                             */
+    DIE_ETIMEOUT = 8,      /* a bounded device-side wait gave up                               */
+    DIE_EUNSUPPORTED = 9   /* FFT size or grid size outside what the kernels handle            */
+} die_status;
+
+typedef enum die_precision {
+    DIE_FP64 = 0,          /* complex128 storage, FP64 arithmetic everywhere                  */
+    DIE_FP32_INNER = 1     /* complex64 FFT products; FP64 for everything else                */
+} die_precision;
+
+typedef struct dieop_s* dieop_t;
+typedef struct defl_s* defl_t;
+
+/* Operator description (Section 4: uniform grid of step h; units of the
+ * background wavelength, so k_b = 2 pi by default). */
+typedef struct dieop_desc {
+    int n1, n2;            /* cells along x1 / x2; 2 <= n <= 4096                              */
+    double h;              /* cell side in background wavelengths, > 0                         */
+    double k_b;            /* background wavenumber; <= 0 selects 2 pi                         */
+    die_precision prec;    /* element type of dieop_apply / dieop_apply_regularized I/O        */
+    int M1, M2;            /* FFT sizes, 0 = smallest 2^a 3^b >= 2 n; else >= 2 n and 2^a 3^b */
+} dieop_desc;
+
+/* dieop_create -- build the operator of Eqs. (4.3)-(4.5) for a permittivity map.
+ *   eps_r: n1*n2 complex128 relative permittivities, layout [x2][x1]; host memory if
+ *          eps_on_device == 0, else device memory.  Copied; the caller keeps ownership.
+ *   Computes the Green's-tensor table and its 2-D FFT (FP64; a complex64 copy is kept
+ *   too), the contrasts chi and chi', and the workspaces.
+ *   Errors: DIE_EINVAL (sizes, h, NULL), DIE_ESINGULAR (|eps_r| <= 1e-12 in some cell:
+ *   the existence condition eps != 0 of Eq. (3.17)), DIE_EUNSUPPORTED (FFT sizes),
+ *   DIE_ENOMEM, DIE_ECUDA.  On error *out is NULL. */
+die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_device,
+                        void* stream, dieop_t* out);
+
+/* Actual sizes chosen at create: out[0..5] = n1, n2, M1, M2, N = n1*n2, prec. */
+die_status dieop_info(dieop_t op, long long* out6);
+
+/* y = A x  (Eq. (4.1) with Eqs. (4.3)-(4.5)); x, y: device, 2*n1*n2 complex of the
+ * type selected by desc.prec (complex128 for DIE_FP64, complex64 for DIE_FP32_INNER).
+ * y may equal x (in place).  Errors: DIE_EINVAL, DIE_ECUDA. */
+die_status dieop_apply(dieop_t op, const void* x, void* y, void* stream);
+
+/* y = A(chi') A(chi) x, the regularised product of Eq. (3.19) / Section 5.
+ * Same types, aliasing and errors as dieop_apply. */
+die_status dieop_apply_regularized(dieop_t op, const void* x, void* y, void* stream);
+
+/* y = A(chi') x alone (the regulariser; used for the right-hand side A_R b). */
+die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* stream);
+
+/* b = incident TE plane wave of unit |E| at angle psi to the x1 axis (Section 4, end):
+ * H3 = exp(i k_b (x1 cos psi + x2 sin psi)), E1 = -sin(psi) H3, E2 = cos(psi) H3.
+ * b: device, 2*n1*n2 complex128.  Errors: DIE_EINVAL, DIE_ECUDA. */
+die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream);
+
+void dieop_destroy(dieop_t op);
+
+/* ----------------------------------------------------------------------------
+ * Restarted GMRES (Sections 4-5) with optional regularisation and deflation.
+ * Solves Atilde x = btilde with Atilde = A (regularized = 0) or A_R A and
+ * btilde = A_R b (regularized = 1), right-preconditioned by the deflation
+ * P^-1 of Eq. (4.12) when a defl_t is given: Atilde P^-1 v = btilde, x = P^-1 v.
+ * Arnoldi by CGS2 (classical Gram-Schmidt with one re-orthogonalisation), FP64;
+ * Hessenberg least squares by Givens rotations, FP64, on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct gmres_opts {
+    int restart;           /* Krylov dimension per cycle, 1..256                               */
+    int max_iters;         /* cap on Arnoldi steps (applications of Atilde)                    */
+    double tol;            /* stop when ||btilde - Atilde x|| / ||btilde|| <= tol              */
+    int regularized;       /* 0: Atilde = A; 1: Atilde = A_R A                                 */
+    int use_x0;            /* 1: x holds the initial guess on entry; 0: x0 = 0                 */
+    die_precision inner;   /* DIE_FP64, or DIE_FP32_INNER: complex64 products inside a cycle,
+                              FP64 restart residual (iterative refinement)                      */
+    int timing;            /* 1: fill t_matvec/t_orth/t_defl (adds stream syncs)               */
+} gmres_opts;
+
+typedef struct gmres_report {
+    int cycles;            /* restart cycles run                                               */
+    int iters;             /* Arnoldi steps = applications of Atilde                           */
+    int n_apply;           /* applications of A or A_R (a regularised step counts 2)           */
+    double rel_res_solved; /* FP64 ||btilde - Atilde x|| / ||btilde|| at exit                  */
+    double rel_res_orig;   /* FP64 ||b - A x|| / ||b|| at exit                                 */
+    double t_matvec, t_orth, t_defl, t_total;   /* seconds                                    */
+    double* history;       /* caller-owned host buffer for per-step residual estimates, or NULL */
+    int history_cap;       /* its length                                                       */
+    int history_len;       /* entries written                                                  */
+} gmres_report;
+
+/* b, x: device complex128, 2*n1*n2.  defl may be NULL.  report may be NULL.
+ * Returns DIE_OK when converged, DIE_ENOCONV at max_iters (x holds the last iterate),
+ * DIE_ENAN if a norm became NaN/Inf, DIE_EBREAKDOWN on a singular Hessenberg system,
+ * DIE_EINVAL on bad options (restart range, defl built for another operator). */
+die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* opts, const void* b, void* x,
+                       gmres_report* report, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Deflation (Eqs. (4.12)-(4.13)): V = orthonormal basis of the invariant subspace
+ * of the r largest-magnitude eigenvalues of Atilde (Krylov-Schur Arnoldi on the
+ * device; the paper uses Matlab eigs with tolerance 1e-4, Section 5), and
+ * T = V^* Atilde V; the preconditioner is P^-1 = I + V (T^-1 - I) V^*.
+ * ------------------------------------------------------------------------- */
+typedef struct defl_opts {
+    int r;                 /* eigenvalues to deflate, 1..128; 0 = count those outside the
+                              deflation radius of Section 5 (capped at r_max)                  */
+    int r_max;             /* cap for r = 0 (default 64 when <= 0)                             */
+    double tol;            /* Ritz residual ||Atilde y - theta y|| <= tol |theta| (1e-4)       */
+    int regularized;       /* deflate A_R A (1) or A (0)                                       */
+    die_precision inner;   /* precision of the products inside the eigensolver               */
+    int krylov_dim;        /* Krylov-Schur basis size; 0 = max(2 r + 16, r + 32)               */
+    int max_restarts;      /* 0 = 200                                                           */
+    unsigned long long seed; /* start vector seed                                              */
+} defl_opts;
+
+/* eig_out: host, 2*r doubles (re, im of the deflated eigenvalues, |.| descending), or
+ * NULL.  r_out (may be NULL) receives the r actually used.  Errors: DIE_EINVAL,
+ * DIE_ENOCONV (not all r Ritz pairs reached tol; the handle is still returned and
+ * usable), DIE_ESINGULAR (T singular), DIE_ENOMEM, DIE_ECUDA. */
+die_status deflation_build(dieop_t op, const defl_opts* opts, void* stream, defl_t* out,
+                           double* eig_out, int* r_out);
+
+/* z = P^-1 x with P^-1 = I + V (T^-1 - I) V^* (Eq. (4.12)); x, z device complex128;
+ * z may equal x. */
+die_status deflation_apply(defl_t defl, const void* x, void* z, void* stream);
+
+void deflation_destroy(defl_t defl);
+
+/* Deflation radius of Section 5: the largest |lambda'| over the images of the segments
+ * [1, eps] under Eq. (5.3), lambda' = [1 + (1 - lambda)/eps] lambda, for every
+ * permittivity value in eps_r (host, count complex128), each segment sampled at
+ * `samples` points (1000 if <= 1).  Returns a negative value on bad arguments. */
+double die_deflation_radius(const double* eps_r, long long count, int samples);
+
+/* ----------------------------------------------------------------------------
+ * Kernel timing (a tracing aid; the paper has no counterpart).  Between
+ * die_prof_begin and die_prof_end every kernel launch of the library is bracketed
+ * by CUDA events on its stream; die_prof_end synchronises the device and sums the
+ * durations per kernel class.  Not thread-safe; do not enable during CUDA-graph
+ * capture.  die_prof_end returns DIE_ENOMEM if the event pool overflowed (the
+ * sums then cover the launches recorded before the overflow).
+ * ------------------------------------------------------------------------- */
+die_status die_prof_begin(void);
+die_status die_prof_end(void);
+int die_prof_kernels(void);                       /* number of kernel classes          */
+const char* die_prof_name(int id);                /* class name, static storage        */
+die_status die_prof_read(int id, long long* launches, double* total_ms);
+
+/* Human-readable name of a status code (static storage). */
+const char* die_status_str(die_status s);
+
+/* Library ABI version (DIE_ABI_VERSION) for binding checks. */
+int die_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBDIE_DIE_H */

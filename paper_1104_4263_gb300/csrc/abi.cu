@@ -1,0 +1,291 @@
+// C ABI entry points of libdie: operator creation (Section 4 discretisation),
+// products with A, A_R and A_R A, the incident plane wave, status strings.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <vector>
+
+#include "op.cuh"
+#include "solver.cuh"
+
+namespace die {
+
+static thread_local char g_last_error[256];
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (getenv("DIE_LOG")) fprintf(stderr, "libdie: %s\n", g_last_error);
+}
+
+die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st);
+die_status compute_contrasts(dieop_s* op, const double2* eps_dev, cudaStream_t st);
+
+// Radices of a Stockham plan for L = 2^a (16 values per thread, radix <= 16) or
+// L = 3 * 2^a (12 values per thread, radix <= 4); stages balanced.
+bool make_plan(int L, FftPlan* p) {
+    int a = 0, b = 0, x = L;
+    if (L < 16) return false;
+    while (x % 2 == 0) { x /= 2; a++; }
+    while (x % 3 == 0) { x /= 3; b++; }
+    if (x != 1 || b > 1) return false;
+    memset(p, 0, sizeof *p);
+    p->L = L;
+    int maxbits = b == 0 ? 4 : 2;
+    p->ept = b == 0 ? 16 : 12;
+    if (b == 1) p->radix[p->ns++] = 3;
+    const int stages = (a + maxbits - 1) / maxbits;
+    const int base = a / stages, extra = a % stages;
+    for (int s = 0; s < stages; s++) {
+        if (p->ns >= kMaxStages) return false;
+        p->radix[p->ns++] = 1 << (base + (s < extra ? 1 : 0));
+    }
+    return true;
+}
+
+static FftPlan reversed(const FftPlan& f) {
+    FftPlan r = f;
+    for (int s = 0; s < f.ns; s++) r.radix[s] = f.radix[f.ns - 1 - s];
+    return r;
+}
+
+int choose_fft_size(int n) {
+    int best = 0;
+    for (int L = 16; L <= 4096; L *= 2) {
+        if (L >= 2 * n) { best = L; break; }
+    }
+    for (int L = 24; L <= 3072; L *= 2) {
+        if (L >= 2 * n && (best == 0 || L < best)) { best = L; break; }
+    }
+    return best;
+}
+
+static void twiddles(int L, std::vector<double2>& d, std::vector<float2>& f) {
+    d.resize(L);
+    f.resize(L);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int m = 0; m < L; m++) {
+        const long double ang = two_pi * (long double)m / (long double)L;
+        const double c = (double)cosl(ang), s = -(double)sinl(ang);
+        d[m] = make_double2(c, s);
+        f[m] = make_float2((float)c, (float)s);
+    }
+}
+
+static std::atomic<uint64_t> g_next_id{1};
+
+}  // namespace die
+
+using namespace die;
+
+static void free_op(dieop_s* op) {
+    if (!op) return;
+    void* ptrs[] = {op->tw1_d, op->tw2_d, op->tw1_f, op->tw2_f, op->gq_d, op->gq_f, op->chi_d, op->chir_d,
+                    op->chi_f, op->chir_f, op->ws.W, op->ws.v, op->dflag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    free_solver_cache(op);
+    delete op;
+}
+
+template <typename P>
+static die_status dmalloc(P** p, size_t bytes) {
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return DIE_ENOMEM; }
+    return DIE_OK;
+}
+
+extern "C" {
+
+int die_abi_version(void) { return DIE_ABI_VERSION; }
+
+const char* die_status_str(die_status s) {
+    switch (s) {
+        case DIE_OK: return "ok";
+        case DIE_EINVAL: return "invalid argument";
+        case DIE_ENOMEM: return "out of memory";
+        case DIE_ECUDA: return "CUDA error";
+        case DIE_ESINGULAR: return "singular: eps_r == 0 in a cell or T singular";
+        case DIE_ENOCONV: return "not converged";
+        case DIE_EBREAKDOWN: return "Arnoldi breakdown";
+        case DIE_ENAN: return "NaN or Inf";
+        case DIE_ETIMEOUT: return "device wait timed out";
+        case DIE_EUNSUPPORTED: return "unsupported size";
+    }
+    return "unknown status";
+}
+
+static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps_on_device, cudaStream_t st,
+                              dieop_s* op) {
+    op->n1 = desc->n1;
+    op->n2 = desc->n2;
+    op->N = desc->n1 * desc->n2;
+    op->h = desc->h;
+    op->k = desc->k_b > 0 ? desc->k_b : 6.283185307179586476925286766559;
+    op->prec = desc->prec;
+    op->M1 = desc->M1 > 0 ? desc->M1 : choose_fft_size(desc->n1);
+    op->M2 = desc->M2 > 0 ? desc->M2 : choose_fft_size(desc->n2);
+    if (op->M1 < 2 * op->n1 || op->M2 < 2 * op->n2) return DIE_EINVAL;
+    if (!make_plan(op->M1, &op->f1) || !make_plan(op->M2, &op->f2)) return DIE_EUNSUPPORTED;
+    if (op->M1 > 4096 || op->M2 > 4096) return DIE_EUNSUPPORTED;
+    op->i1 = reversed(op->f1);
+    op->i2 = reversed(op->f2);
+    op->Q1 = op->M1 / 2 + 1;
+    op->Q2 = op->M2 / 2 + 1;
+    DIE_CUDA_TRY(cudaGetDevice(&op->device));
+    const long N = op->N, q = (long)op->Q1 * op->Q2;
+    DIE_TRY(dmalloc(&op->tw1_d, op->M1 * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->tw2_d, op->M2 * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->tw1_f, op->M1 * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->tw2_f, op->M2 * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->gq_d, 3 * q * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->gq_f, 3 * q * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->chi_d, N * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->chir_d, N * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->chi_f, N * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->chir_f, N * sizeof(float2)));
+    op->ws.W_bytes = 2 * (size_t)op->M1 * op->n2 * sizeof(double2);
+    op->ws.v_bytes = 2 * (size_t)N * sizeof(double2);
+    DIE_TRY(dmalloc(&op->ws.W, op->ws.W_bytes));
+    DIE_TRY(dmalloc(&op->ws.v, op->ws.v_bytes));
+    DIE_TRY(dmalloc(&op->dflag, sizeof(int)));
+    DIE_CUDA_TRY(cudaMemsetAsync(op->dflag, 0, sizeof(int), st));
+    DIE_TRY(set_kernel_attributes(op));
+
+    std::vector<double2> t1d, t2d;
+    std::vector<float2> t1f, t2f;
+    twiddles(op->M1, t1d, t1f);
+    twiddles(op->M2, t2d, t2f);
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_d, t1d.data(), op->M1 * sizeof(double2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_d, t2d.data(), op->M2 * sizeof(double2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_f, t1f.data(), op->M1 * sizeof(float2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_f, t2f.data(), op->M2 * sizeof(float2), cudaMemcpyHostToDevice, st));
+
+    double2* scratch = nullptr;
+    const size_t scratch_bytes = 3 * (size_t)op->M1 * op->M2 * sizeof(double2) + (eps_on_device ? 0 : N * sizeof(double2));
+    DIE_TRY(dmalloc(&scratch, scratch_bytes));
+    const double2* eps_dev = (const double2*)eps_r;
+    if (!eps_on_device) {
+        double2* e = scratch + 3 * (size_t)op->M1 * op->M2;
+        die_status s = DIE_OK;
+        if (cudaMemcpyAsync(e, eps_r, N * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess) s = DIE_ECUDA;
+        if (s != DIE_OK) { cudaFree(scratch); return s; }
+        eps_dev = e;
+    }
+    die_status s = compute_contrasts(op, eps_dev, st);
+    if (s == DIE_OK) s = build_green_spectrum(op, scratch, st);
+    int flag = 0;
+    if (s == DIE_OK && cudaMemcpyAsync(&flag, op->dflag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) s = DIE_ECUDA;
+    if (s == DIE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = DIE_ECUDA;
+    cudaFree(scratch);
+    if (s != DIE_OK) return s;
+    if (flag) return DIE_ESINGULAR;
+    op->id = g_next_id.fetch_add(1);
+    return DIE_OK;
+}
+
+die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_device, void* stream, dieop_t* out) {
+    if (!out) return DIE_EINVAL;
+    *out = nullptr;
+    if (!desc || !eps_r) return DIE_EINVAL;
+    if (desc->n1 < 2 || desc->n2 < 2 || desc->n1 > 2048 || desc->n2 > 2048) return DIE_EINVAL;
+    if (!(desc->h > 0) || !isfinite(desc->h)) return DIE_EINVAL;
+    if (desc->prec != DIE_FP64 && desc->prec != DIE_FP32_INNER) return DIE_EINVAL;
+    dieop_s* op = new (std::nothrow) dieop_s();
+    if (!op) return DIE_ENOMEM;
+    die_status s = create_impl(desc, eps_r, eps_on_device, (cudaStream_t)stream, op);
+    if (s != DIE_OK) { free_op(op); return s; }
+    *out = op;
+    return DIE_OK;
+}
+
+die_status dieop_info(dieop_t op, long long* o) {
+    if (!op || !o) return DIE_EINVAL;
+    o[0] = op->n1; o[1] = op->n2; o[2] = op->M1; o[3] = op->M2; o[4] = op->N; o[5] = op->prec;
+    return DIE_OK;
+}
+
+void dieop_destroy(dieop_t op) {
+    if (!op) return;
+    cudaDeviceSynchronize();
+    free_op(op);
+}
+
+static die_status apply_any(dieop_t op, const void* x, void* y, void* stream, int kind) {
+    if (!op || !x || !y) return DIE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (op->prec == DIE_FP64) {
+        const double2* xi = (const double2*)x;
+        double2* yo = (double2*)y;
+        if (kind == 0) return apply_op<double, double2>(op, Contrast::Chi, xi, yo, st);
+        if (kind == 1) return apply_reg<double, double2>(op, xi, yo, st);
+        return apply_op<double, double2>(op, Contrast::ChiReg, xi, yo, st);
+    }
+    const float2* xi = (const float2*)x;
+    float2* yo = (float2*)y;
+    if (kind == 0) return apply_op<float, float2>(op, Contrast::Chi, xi, yo, st);
+    if (kind == 1) return apply_reg<float, float2>(op, xi, yo, st);
+    return apply_op<float, float2>(op, Contrast::ChiReg, xi, yo, st);
+}
+
+die_status dieop_apply(dieop_t op, const void* x, void* y, void* stream) { return apply_any(op, x, y, stream, 0); }
+die_status dieop_apply_regularized(dieop_t op, const void* x, void* y, void* stream) {
+    return apply_any(op, x, y, stream, 1);
+}
+die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* stream) {
+    return apply_any(op, x, y, stream, 2);
+}
+
+}  // extern "C"
+
+// Incident TE plane wave (Section 4, end; component labels read so that the
+// source-free TE equations of Eq. (2.1) hold): H3 = exp(i k (x1 cos psi + x2 sin psi)),
+// E1 = -sin(psi) H3, E2 = cos(psi) H3, at cell centres x_i = (i + 1/2) h - n h / 2.
+__global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi, double2* b) {
+    const long N = (long)n1 * n2;
+    double sp, cp;
+    sincos(psi, &sp, &cp);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const int i1 = (int)(i % n1), i2 = (int)(i / n1);
+        const double x1 = (i1 + 0.5) * h - 0.5 * n1 * h;
+        const double x2 = (i2 + 0.5) * h - 0.5 * n2 * h;
+        double s, c;
+        sincos(k * (x1 * cp + x2 * sp), &s, &c);
+        b[i] = make_double2(-sp * c, -sp * s);
+        b[N + i] = make_double2(cp * c, cp * s);
+    }
+}
+
+extern "C" die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream) {
+    if (!op || !b || !isfinite(psi)) return DIE_EINVAL;
+    plane_wave_kernel<<<608, 256, 0, (cudaStream_t)stream>>>(op->n1, op->n2, op->h, op->k, psi, (double2*)b);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+// Section 5: radius of the smallest circle around 0 that holds the images of all
+// segments [1, eps] under lambda' = [1 + (1 - lambda)/eps] lambda (Eq. (5.3)).
+extern "C" double die_deflation_radius(const double* eps_r, long long count, int samples) {
+    if (!eps_r || count <= 0) return -1.0;
+    if (samples <= 1) samples = 1000;
+    double R = 0.0;
+    for (long long i = 0; i < count; i++) {
+        const double er = eps_r[2 * i], ei = eps_r[2 * i + 1];
+        const double m2 = er * er + ei * ei;
+        if (!(m2 > 0)) return -1.0;
+        if (i > 0 && er == eps_r[2 * i - 2] && ei == eps_r[2 * i - 1]) continue;   // repeated value
+        for (int sidx = 0; sidx < samples; sidx++) {
+            const double t = (double)sidx / (samples - 1);
+            const double lr = 1.0 + t * (er - 1.0), li = t * ei;        // lambda on [1, eps]
+            // (1 - lambda) / eps
+            const double ar = 1.0 - lr, ai = -li;
+            const double qr = (ar * er + ai * ei) / m2, qi = (ai * er - ar * ei) / m2;
+            // (1 + q) lambda
+            const double pr = (1.0 + qr) * lr - qi * li, pi = (1.0 + qr) * li + qi * lr;
+            const double mag = sqrt(pr * pr + pi * pi);
+            if (mag > R) R = mag;
+        }
+    }
+    return R;
+}

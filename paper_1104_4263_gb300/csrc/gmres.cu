@@ -1,0 +1,296 @@
+// Restarted GMRES(m) (Saad & Schultz) on Atilde = A or A_R A (Section 5), with the
+// deflating right preconditioner of Eq. (4.12): Atilde P^-1 v = btilde, x = P^-1 v.
+//
+// One cycle runs entirely on the device without host round trips: the Arnoldi
+// vectors are orthogonalised by CGS2 (three fused sweeps: projections;
+// update + re-projection; update + norm), the new column of the Hessenberg matrix
+// is rotated by Givens rotations on the device, and when the residual estimate
+// reaches tol a device flag makes the remaining kernels of the cycle return at
+// once.  The host reads one flag set per cycle.  Between cycles the residual
+// btilde - Atilde x is recomputed in FP64 (in the FP32-inner form this is the
+// iterative-refinement step).
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "solver.cuh"
+
+namespace die {
+
+die_status alloc_red_scratch(RedScratch* rs) {
+    if (cudaMalloc((void**)&rs->partial, (size_t)kMaxBasis * kRedBlocks * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return DIE_ENOMEM;
+    }
+    if (cudaMalloc((void**)&rs->counter, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return DIE_ENOMEM;
+    }
+    DIE_CUDA_TRY(cudaMemset(rs->counter, 0, sizeof(unsigned)));
+    return DIE_OK;
+}
+
+void free_red_scratch(RedScratch* rs) {
+    if (rs->partial) cudaFree(rs->partial);
+    if (rs->counter) cudaFree(rs->counter);
+    rs->partial = nullptr;
+    rs->counter = nullptr;
+}
+
+SolverCache* solver_cache(dieop_s* op) { return reinterpret_cast<SolverCache*>(op->solver); }
+
+void free_solver_cache(dieop_s* op) {
+    SolverCache* c = solver_cache(op);
+    if (!c) return;
+    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->small, c->hist, c->ints, c->wnorm, c->one};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    free_red_scratch(&c->rs);
+    if (c->host) cudaFreeHost(c->host);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+    op->solver = nullptr;
+}
+
+static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 4 * (m + 2) + 8; }
+
+die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
+    SolverCache* c = solver_cache(op);
+    const long n = 2L * op->N;
+    if (c && c->m_cap >= m && c->hist_cap >= hist_cap) return DIE_OK;
+    if (c) {
+        m = m > c->m_cap ? m : c->m_cap;
+        hist_cap = hist_cap > c->hist_cap ? hist_cap : c->hist_cap;
+        free_solver_cache(op);
+    }
+    c = new SolverCache();
+    op->solver = c;
+    c->m_cap = m;
+    c->n = n;
+    c->hist_cap = hist_cap;
+    auto al = [](void** p, size_t b) { return cudaMalloc(p, b) == cudaSuccess; };
+    bool ok = al((void**)&c->V, (size_t)(m + 1) * n * sizeof(double2)) && al((void**)&c->btil, n * sizeof(double2)) &&
+              al((void**)&c->tmp, n * sizeof(double2)) && al((void**)&c->z, n * sizeof(double2)) &&
+              al((void**)&c->small, small_count(m) * sizeof(double2)) &&
+              al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) && al((void**)&c->ints, 8 * sizeof(int)) &&
+              al((void**)&c->wnorm, 8 * sizeof(double)) && al((void**)&c->one, sizeof(double2));
+    if (!ok) {
+        cudaGetLastError();
+        free_solver_cache(op);
+        return DIE_ENOMEM;
+    }
+    DIE_TRY(alloc_red_scratch(&c->rs));
+    if (cudaHostAlloc((void**)&c->host, 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        free_solver_cache(op);
+        return DIE_ENOMEM;
+    }
+    const double2 one = make_double2(1.0, 0.0);
+    DIE_CUDA_TRY(cudaMemcpy(c->one, &one, sizeof one, cudaMemcpyHostToDevice));
+    c->ev.resize(4 * (size_t)(m + 1));
+    for (auto& e : c->ev) DIE_CUDA_TRY(cudaEventCreate(&e));
+    return DIE_OK;
+}
+
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st) {
+    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, d->s, d->rs, skip, st));
+    DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
+    return DIE_OK;
+}
+
+// Atilde in FP64 (restart residuals, right-hand side).
+static die_status apply64(dieop_s* op, bool reg, const double2* in, double2* out, cudaStream_t st) {
+    return reg ? apply_reg<double, double2>(op, in, out, st) : apply_op<double, double2>(op, Contrast::Chi, in, out, st);
+}
+
+static die_status apply_inner(dieop_s* op, bool reg, bool mixed, const double2* in, double2* out, const int* skip,
+                              cudaStream_t st) {
+    if (mixed)
+        return reg ? apply_reg_skip<float, double2>(op, in, out, skip, st)
+                   : apply_op_skip<float, double2>(op, Contrast::Chi, in, out, skip, st);
+    return reg ? apply_reg_skip<double, double2>(op, in, out, skip, st)
+               : apply_op_skip<double, double2>(op, Contrast::Chi, in, out, skip, st);
+}
+
+// ||v||^2 read back to the host (synchronises the stream).
+static die_status norm2_host(SolverCache* c, const double2* v, long n, double2* dev_out, double* host_out,
+                             cudaStream_t st) {
+    DIE_TRY(k_dots(v, 0, 1, v, n, dev_out, c->rs, nullptr, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(c->host, dev_out, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DIE_CUDA_TRY(cudaStreamSynchronize(st));
+    *host_out = c->host[0];
+    return DIE_OK;
+}
+
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace die
+
+using namespace die;
+
+extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, const void* b_, void* x_,
+                                  gmres_report* rep, void* stream) {
+    if (!op || !o || !b_ || !x_) return DIE_EINVAL;
+    if (o->restart < 1 || o->restart > 256 || o->max_iters < 0 || !(o->tol >= 0)) return DIE_EINVAL;
+    if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return DIE_EINVAL;
+    if (defl && (defl->op_id != op->id || defl->regularized != (o->regularized ? 1 : 0))) return DIE_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
+    const int m = o->restart;
+    const long n = 2L * op->N;
+    const int hist_cap = o->max_iters < (1 << 22) ? (o->max_iters > 0 ? o->max_iters : 1) : (1 << 22);
+    DIE_TRY(ensure_solver_cache(op, m, hist_cap));
+    SolverCache* c = solver_cache(op);
+    const double2* b = (const double2*)b_;
+    double2* x = (double2*)x_;
+
+    // device state of a cycle
+    double2* sm = c->small;
+    GmresDev S;
+    S.H = sm; sm += (size_t)(m + 1) * m;
+    S.cs = sm; sm += m;
+    S.sn = sm; sm += m;
+    S.g = sm; sm += m + 2;
+    S.h1 = sm; sm += m + 2;
+    S.h2 = sm; sm += m + 2;
+    S.y = sm; sm += m + 2;
+    double2* scal = sm;            // scalars: [0] residual norm^2
+    S.hist = c->hist;
+    S.done = c->ints;
+    S.k = c->ints + 1;
+    S.flags = c->ints + 2;
+    S.wnorm = c->wnorm;
+    S.m = m;
+    S.hist_cap = c->hist_cap;
+    S.tol = o->tol;
+    DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, 8 * sizeof(int), st));
+
+    // right-hand side of the solved system
+    const double2* bt = b;
+    int n_apply = 0;
+    if (reg) {
+        DIE_TRY(apply_op<double, double2>(op, Contrast::ChiReg, b, c->btil, st));
+        bt = c->btil;
+        n_apply++;
+    }
+    double bn2 = 0;
+    DIE_TRY(norm2_host(c, bt, n, scal, &bn2, st));
+    const double bnorm = sqrt(bn2);
+    if (!isfinite(bnorm)) return DIE_ENAN;
+    if (!o->use_x0) DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+    S.bnorm = bnorm > 0 ? bnorm : 1.0;
+
+    die_status status = DIE_ENOCONV;
+    int iters = 0, cycles = 0, hist_len = 0;
+    double rel = 0, t_mv = 0, t_orth = 0, t_defl = 0;
+    const long ldv = n;
+    double2* V = c->V;
+    if (bnorm == 0.0) {
+        DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+        status = DIE_OK;
+    }
+    while (status == DIE_ENOCONV) {
+        // r = btilde - Atilde x in FP64 into V_0
+        if (cycles == 0 && !o->use_x0) {
+            DIE_CUDA_TRY(cudaMemcpyAsync(V, bt, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        } else {
+            DIE_TRY(apply64(op, reg, x, c->tmp, st));
+            n_apply += reg ? 2 : 1;
+            DIE_TRY(k_sub(bt, c->tmp, V, n, st));
+        }
+        double beta2 = 0;
+        DIE_TRY(norm2_host(c, V, n, scal, &beta2, st));
+        rel = sqrt(beta2) / bnorm;
+        if (!isfinite(rel)) { status = DIE_ENAN; break; }
+        if (rel <= o->tol) { status = DIE_OK; break; }
+        if (iters >= o->max_iters) break;
+        DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st));
+        DIE_TRY(k_gmres_init(S, scal, st));
+        const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
+        S.jmax = jmax;
+        for (int j = 0; j < jmax; j++) {
+            const double2* vj = V + (long)j * ldv;
+            double2* w = V + (long)(j + 1) * ldv;
+            if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j], st));
+            const double2* src = vj;
+            if (defl) {
+                DIE_TRY(defl_apply(defl, vj, c->z, S.done, st));
+                src = c->z;
+            }
+            if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
+            DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st));
+            if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
+            DIE_TRY(k_dots(V, ldv, j + 2, w, n, S.h1, c->rs, S.done, st));
+            DIE_TRY(k_cgs_update_dots(V, ldv, j + 1, w, n, S.h1, S.h2, c->rs, S.done, st));
+            DIE_TRY(k_cgs_update_norm_givens(V, ldv, j + 1, w, n, S, j, iters + j, c->rs, st));
+            DIE_TRY(k_scale_inv_real(w, n, S.wnorm, S.done, st));
+            if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
+        }
+        int hk[4];
+        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DIE_CUDA_TRY(cudaStreamSynchronize(st));
+        memcpy(hk, c->host, sizeof hk);
+        const int k = hk[1], flags = hk[2];
+        if (o->timing) {
+            for (int j = 0; j < k; j++) {
+                float a = 0, bb = 0, cc = 0;
+                cudaEventElapsedTime(&a, c->ev[4 * j], c->ev[4 * j + 1]);
+                cudaEventElapsedTime(&bb, c->ev[4 * j + 1], c->ev[4 * j + 2]);
+                cudaEventElapsedTime(&cc, c->ev[4 * j + 2], c->ev[4 * j + 3]);
+                t_defl += a * 1e-3; t_mv += bb * 1e-3; t_orth += cc * 1e-3;
+            }
+        }
+        iters += k;
+        n_apply += k * (reg ? 2 : 1);
+        hist_len = iters < c->hist_cap ? iters : c->hist_cap;
+        cycles++;
+        if (flags & 1) { status = DIE_ENAN; break; }
+        if (k == 0) { status = DIE_EBREAKDOWN; break; }
+        DIE_TRY(k_gmres_lsq(S, st));
+        if (defl) {
+            DIE_TRY(k_lincomb(V, ldv, k, S.y, c->tmp, n, st));
+            DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st));
+            DIE_TRY(k_lincomb_add(c->tmp, ldv, 1, c->one, x, n, st));
+        } else {
+            DIE_TRY(k_lincomb_add(V, ldv, k, S.y, x, n, st));
+        }
+        // a singular triangular factor (breakdown with no exact solution) shows up after the LSQ
+        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DIE_CUDA_TRY(cudaStreamSynchronize(st));
+        memcpy(hk, c->host, sizeof hk);
+        if (hk[2] & 4) { status = DIE_EBREAKDOWN; break; }
+    }
+    double rel_orig = rel;
+    if (reg && (status == DIE_OK || status == DIE_ENOCONV)) {
+        DIE_TRY(apply_op<double, double2>(op, Contrast::Chi, x, c->tmp, st));
+        n_apply++;
+        DIE_TRY(k_sub(b, c->tmp, c->tmp, n, st));
+        double r2 = 0, b2 = 0;
+        DIE_TRY(norm2_host(c, c->tmp, n, scal, &r2, st));
+        DIE_TRY(norm2_host(c, b, n, scal, &b2, st));
+        rel_orig = b2 > 0 ? sqrt(r2 / b2) : 0.0;
+    }
+    DIE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->cycles = cycles;
+        rep->iters = iters;
+        rep->n_apply = n_apply;
+        rep->rel_res_solved = rel;
+        rep->rel_res_orig = rel_orig;
+        rep->t_matvec = t_mv;
+        rep->t_orth = t_orth;
+        rep->t_defl = t_defl;
+        rep->t_total = seconds_since(t0);
+        rep->history_len = 0;
+        if (rep->history && rep->history_cap > 0 && hist_len > 0) {
+            const int cnt = hist_len < rep->history_cap ? hist_len : rep->history_cap;
+            DIE_CUDA_TRY(cudaMemcpy(rep->history, c->hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+            rep->history_len = cnt;
+        }
+    }
+    return status;
+}

@@ -1,0 +1,69 @@
+// Operator handle of libdie and the device view passed to the FFT-convolution kernels.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace die {
+
+// Everything a product kernel needs, by value.
+template <typename T>
+struct OpDev {
+    using C = C_t<T>;
+    int n1, n2, M1, M2, Q1, Q2;   // grid, FFT sizes, quarter-spectrum extents (M/2 + 1)
+    FftPlan f1, i1, f2, i2;       // forward / inverse plans along x1 (length M1) and x2 (M2)
+    const C* tw1;                 // exp(-2 pi i m / M1), m < M1
+    const C* tw2;                 // exp(-2 pi i m / M2)
+    const C* gq;                  // quarter spectra of G11, G22, G12: [plane][k1q][k2q], pre-scaled
+};
+
+struct Workspace {
+    void* W = nullptr;            // 2 x M1 x n2 complex (compute precision), transposed row spectra
+    void* v = nullptr;            // 2 x N complex: intermediate of the regularised product
+    size_t W_bytes = 0, v_bytes = 0;
+};
+
+}  // namespace die
+
+struct dieop_s {
+    int device = 0;
+    int n1 = 0, n2 = 0, M1 = 0, M2 = 0, N = 0, Q1 = 0, Q2 = 0;
+    double h = 0, k = 0;
+    die_precision prec = DIE_FP64;
+    die::FftPlan f1{}, i1{}, f2{}, i2{};
+    double2 *tw1_d = nullptr, *tw2_d = nullptr;
+    float2 *tw1_f = nullptr, *tw2_f = nullptr;
+    double2* gq_d = nullptr;       // 3 * Q1 * Q2
+    float2* gq_f = nullptr;
+    double2 *chi_d = nullptr, *chir_d = nullptr;   // chi = eps_r - 1, chi' = 1/eps_r - 1
+    float2 *chi_f = nullptr, *chir_f = nullptr;
+    die::Workspace ws;             // FP64-sized; the complex64 path uses the first half
+    int* dflag = nullptr;          // device status word (create-time checks)
+    uint64_t id = 0;               // identity for deflation handles
+    void* solver = nullptr;        // die::SolverCache, created by the first gmres_solve
+};
+
+namespace die {
+
+OpDev<double> view_d(const dieop_s* op);
+OpDev<float> view_f(const dieop_s* op);
+
+enum class Contrast { Chi, ChiReg };
+
+// y = (I - G X(contrast)) x with compute type T and element type IO for x and y.
+template <typename T, typename IO>
+die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st);
+
+// y = A(chi') A(chi) x.
+template <typename T, typename IO>
+die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st);
+
+// The same with a device flag: every kernel returns at once when *skip != 0.
+template <typename T, typename IO>
+die_status apply_op_skip(dieop_s* op, Contrast c, const IO* x, IO* y, const int* skip, cudaStream_t st);
+template <typename T, typename IO>
+die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st);
+
+die_status set_kernel_attributes(const dieop_s* op);
+
+}  // namespace die

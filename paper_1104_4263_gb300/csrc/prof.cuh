@@ -1,0 +1,36 @@
+// Kernel timing aid: while enabled (die_prof_begin .. die_prof_end), every kernel
+// launch of the library is bracketed by CUDA events recorded on its stream; the
+// durations are summed per kernel class when the session ends.  Off by default.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace die {
+
+enum ProfKernel {
+    PK_ROWS_FWD = 0,      // K1: contrast multiply + row FFT
+    PK_COLS,              // K2: column FFT, Green-spectrum multiply, inverse column FFT
+    PK_ROWS_INV,          // K3: row inverse FFT + crop + subtract
+    PK_ROWS_INV_FWD,      // K3K1: fused row inverse of A(chi) and row forward of A(chi')
+    PK_DOTS,              // batched projections V^* w
+    PK_UPDATE_DOTS,       // CGS2 sweep 2: w -= V h, projections again
+    PK_UPDATE_NORM,       // CGS2 sweep 3: w -= V h, norm (+ Givens step)
+    PK_SCALE,             // vector scaling
+    PK_DEFL_UPDATE,       // deflation z = x + V (M s)
+    PK_LINCOMB,           // x += V y
+    PK_SMALL,             // single-thread small dense work
+    PK_OTHER,
+    PK_COUNT
+};
+
+extern bool g_prof_on;
+void prof_mark(int id, cudaStream_t st, int stop);
+
+}  // namespace die
+
+#define DIE_PROF(id, st, ...)                                  \
+    do {                                                       \
+        if (die::g_prof_on) die::prof_mark((id), (st), 0);     \
+        __VA_ARGS__;                                           \
+        if (die::g_prof_on) die::prof_mark((id), (st), 1);     \
+    } while (0)

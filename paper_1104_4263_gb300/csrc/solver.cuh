@@ -1,0 +1,54 @@
+// Workspaces of restarted GMRES and the deflation handle.
+#pragma once
+
+#include <vector>
+
+#include "krylov.cuh"
+#include "op.cuh"
+
+namespace die {
+
+// Device buffers reused across gmres_solve calls on one operator.
+struct SolverCache {
+    int m_cap = 0;          // Krylov dimension the buffers hold
+    long n = 0;             // vector length 2N
+    int hist_cap = 0;
+    double2* V = nullptr;   // (m_cap + 1) * n
+    double2* btil = nullptr;
+    double2* tmp = nullptr;
+    double2* z = nullptr;
+    double2* small = nullptr;   // H, cs, sn, g, h1, h2, y, scalars
+    double* hist = nullptr;
+    int* ints = nullptr;        // done, k, flags
+    double* wnorm = nullptr;
+    double2* one = nullptr;     // device constant 1 + 0i
+    RedScratch rs;
+    double* host = nullptr;     // pinned readback area
+    std::vector<cudaEvent_t> ev;
+};
+
+void free_solver_cache(dieop_s* op);
+SolverCache* solver_cache(dieop_s* op);
+die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap);
+die_status alloc_red_scratch(RedScratch* rs);
+void free_red_scratch(RedScratch* rs);
+
+}  // namespace die
+
+// Deflation handle: V (r orthonormal vectors of length n) and M = T^-1 - I (Eq. (4.12)).
+struct defl_s {
+    uint64_t op_id = 0;
+    int r = 0;
+    long n = 0;
+    int regularized = 0;
+    double2* V = nullptr;       // r * n, vector i at V + i * n
+    double2* M = nullptr;       // r * r, column-major
+    double2* s = nullptr;       // r projections (scratch)
+    die::RedScratch rs;
+    std::vector<double> eigs;   // (re, im) pairs, |lambda| descending
+};
+
+namespace die {
+// z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip` as for the Krylov kernels.
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st);
+}  // namespace die

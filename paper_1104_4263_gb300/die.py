@@ -1,0 +1,305 @@
+"""Thin Python binding of libdie (ctypes): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts
+PyTorch tensors to device pointers and streams, and C status codes to exceptions.
+It never falls back to any other implementation: if the library is missing or the
+GPU is absent, the calls raise.
+
+Vectors are torch tensors on the current CUDA device, shape (2, n2, n1) (or flat
+2*n1*n2), dtype complex128 (or complex64 for the FP32 operator products).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+from .build import LIB
+
+DIE_FP64 = 0
+DIE_FP32_INNER = 1
+
+STATUS = {0: "DIE_OK", 1: "DIE_EINVAL", 2: "DIE_ENOMEM", 3: "DIE_ECUDA", 4: "DIE_ESINGULAR",
+          5: "DIE_ENOCONV", 6: "DIE_EBREAKDOWN", 7: "DIE_ENAN", 8: "DIE_ETIMEOUT", 9: "DIE_EUNSUPPORTED"}
+
+
+class DieError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({_lib().die_status_str(code).decode()})")
+
+
+class Desc(ct.Structure):
+    _fields_ = [("n1", ct.c_int), ("n2", ct.c_int), ("h", ct.c_double), ("k_b", ct.c_double),
+                ("prec", ct.c_int), ("M1", ct.c_int), ("M2", ct.c_int)]
+
+
+class GmresOpts(ct.Structure):
+    _fields_ = [("restart", ct.c_int), ("max_iters", ct.c_int), ("tol", ct.c_double), ("regularized", ct.c_int),
+                ("use_x0", ct.c_int), ("inner", ct.c_int), ("timing", ct.c_int)]
+
+
+class GmresReport(ct.Structure):
+    _fields_ = [("cycles", ct.c_int), ("iters", ct.c_int), ("n_apply", ct.c_int),
+                ("rel_res_solved", ct.c_double), ("rel_res_orig", ct.c_double),
+                ("t_matvec", ct.c_double), ("t_orth", ct.c_double), ("t_defl", ct.c_double),
+                ("t_total", ct.c_double), ("history", ct.POINTER(ct.c_double)), ("history_cap", ct.c_int),
+                ("history_len", ct.c_int)]
+
+
+class DeflOpts(ct.Structure):
+    _fields_ = [("r", ct.c_int), ("r_max", ct.c_int), ("tol", ct.c_double), ("regularized", ct.c_int),
+                ("inner", ct.c_int), ("krylov_dim", ct.c_int), ("max_restarts", ct.c_int),
+                ("seed", ct.c_ulonglong)]
+
+
+EXPORTS = {
+    "dieop_create": (ct.c_int, [ct.POINTER(Desc), ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "dieop_info": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
+    "dieop_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "dieop_apply_regularized": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "dieop_apply_regularizer": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "dieop_rhs_plane_wave": (ct.c_int, [ct.c_void_p, ct.c_double, ct.c_void_p, ct.c_void_p]),
+    "dieop_destroy": (None, [ct.c_void_p]),
+    "gmres_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p, ct.c_void_p,
+                               ct.POINTER(GmresReport), ct.c_void_p]),
+    "deflation_build": (ct.c_int, [ct.c_void_p, ct.POINTER(DeflOpts), ct.c_void_p, ct.POINTER(ct.c_void_p),
+                                   ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
+    "deflation_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "deflation_destroy": (None, [ct.c_void_p]),
+    "die_deflation_radius": (ct.c_double, [ct.c_void_p, ct.c_longlong, ct.c_int]),
+    "die_prof_begin": (ct.c_int, []),
+    "die_prof_end": (ct.c_int, []),
+    "die_prof_kernels": (ct.c_int, []),
+    "die_prof_name": (ct.c_char_p, [ct.c_int]),
+    "die_prof_read": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_double)]),
+    "die_status_str": (ct.c_char_p, [ct.c_int]),
+    "die_abi_version": (ct.c_int, []),
+}
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libdie is not built ({LIB} missing): run __graft_entry__.build() "
+                               "or python -m paper_1104_4263_gb300.build")
+        lib = ct.CDLL(LIB)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        if lib.die_abi_version() != 1:
+            raise RuntimeError("libdie ABI version mismatch")
+        _LIB = lib
+    return _LIB
+
+
+def lib():
+    """The loaded ctypes library (loads it on first use)."""
+    return _lib()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise DieError(code, what)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if not t.is_cuda:
+        raise ValueError("libdie takes CUDA tensors (device memory)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ct.c_void_p(t.data_ptr())
+
+
+def deflation_radius(eps_r) -> float:
+    """Section 5 deflation radius for a permittivity map (numpy complex array)."""
+    import numpy as np
+    e = np.ascontiguousarray(np.asarray(eps_r, dtype=np.complex128).reshape(-1))
+    return float(_lib().die_deflation_radius(e.ctypes.data_as(ct.c_void_p), e.size, 1000))
+
+
+class KernelTimer:
+    """Context manager: per-kernel-class launch counts and total milliseconds
+    (CUDA events around every library launch inside the block)."""
+
+    def __enter__(self):
+        _check(_lib().die_prof_begin(), "die_prof_begin")
+        self.result = {}
+        return self
+
+    def __exit__(self, *exc):
+        code = _lib().die_prof_end()
+        L = _lib()
+        for i in range(L.die_prof_kernels()):
+            n = ct.c_longlong()
+            ms = ct.c_double()
+            _check(L.die_prof_read(i, ct.byref(n), ct.byref(ms)), "die_prof_read")
+            if n.value:
+                self.result[L.die_prof_name(i).decode()] = {"launches": n.value, "ms": ms.value}
+        self.overflow = code != 0
+        return False
+
+
+class Operator:
+    """The discretised TE operator A = I - G X on an n1 x n2 grid (a dieop_t handle)."""
+
+    def __init__(self, eps_r, h: float, k_b: float = 2 * math.pi, prec: int = DIE_FP64,
+                 M1: int = 0, M2: int = 0, stream=None):
+        import numpy as np
+        import torch
+        eps = eps_r
+        if isinstance(eps, torch.Tensor):
+            eps_t = eps.to(torch.complex128).contiguous()
+            n2, n1 = eps_t.shape
+            on_dev = 1 if eps_t.is_cuda else 0
+            if not on_dev:
+                eps_np = eps_t.numpy()
+        else:
+            eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128))
+            n2, n1 = eps_np.shape
+            on_dev = 0
+        self.n1, self.n2, self.h, self.k_b, self.prec = n1, n2, h, k_b, prec
+        desc = Desc(n1, n2, h, k_b, prec, M1, M2)
+        handle = ct.c_void_p()
+        ptr = _ptr(eps_t) if on_dev else eps_np.ctypes.data_as(ct.c_void_p)
+        _check(_lib().dieop_create(ct.byref(desc), ptr, on_dev, _stream(stream), ct.byref(handle)), "dieop_create")
+        self._h = handle
+        info = (ct.c_longlong * 6)()
+        _check(_lib().dieop_info(self._h, info), "dieop_info")
+        self.M1, self.M2 = int(info[2]), int(info[3])
+        self.N = n1 * n2
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().dieop_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _io_dtype(self):
+        import torch
+        return torch.complex128 if self.prec == DIE_FP64 else torch.complex64
+
+    def _out(self, x, y):
+        import torch
+        if x.dtype != self._io_dtype():
+            raise TypeError(f"expected {self._io_dtype()}, got {x.dtype}")
+        if x.numel() != 2 * self.N:
+            raise ValueError("vector must hold 2 * n1 * n2 complex values")
+        return torch.empty_like(x) if y is None else y
+
+    def apply(self, x, y=None, stream=None):
+        """y = A x (Eqs. (4.1)-(4.5))."""
+        y = self._out(x, y)
+        _check(_lib().dieop_apply(self._h, _ptr(x), _ptr(y), _stream(stream)), "dieop_apply")
+        return y
+
+    def apply_regularized(self, x, y=None, stream=None):
+        """y = A(chi') A(chi) x (Eq. (3.19), Section 5)."""
+        y = self._out(x, y)
+        _check(_lib().dieop_apply_regularized(self._h, _ptr(x), _ptr(y), _stream(stream)), "dieop_apply_regularized")
+        return y
+
+    def apply_regularizer(self, x, y=None, stream=None):
+        """y = A(chi') x."""
+        y = self._out(x, y)
+        _check(_lib().dieop_apply_regularizer(self._h, _ptr(x), _ptr(y), _stream(stream)), "dieop_apply_regularizer")
+        return y
+
+    def plane_wave(self, psi: float, out=None, stream=None):
+        """Incident TE plane wave at angle psi (complex128, shape (2, n2, n1))."""
+        import torch
+        b = torch.empty((2, self.n2, self.n1), dtype=torch.complex128, device="cuda") if out is None else out
+        _check(_lib().dieop_rhs_plane_wave(self._h, float(psi), _ptr(b), _stream(stream)), "dieop_rhs_plane_wave")
+        return b
+
+    def solve(self, b, x=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
+              regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
+              timing: bool = False, history: int = 0, stream=None, raise_on_noconv: bool = False):
+        """Restarted GMRES; returns (x, report dict).  x (complex128) may hold an initial guess."""
+        import numpy as np
+        import torch
+        if b.dtype != torch.complex128:
+            raise TypeError("solve takes complex128 vectors")
+        use_x0 = x is not None
+        if x is None:
+            x = torch.empty_like(b)
+        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, int(bool(timing)))
+        rep = GmresReport()
+        hist = None
+        if history > 0:
+            hist = np.zeros(history, dtype=np.float64)
+            rep.history = hist.ctypes.data_as(ct.POINTER(ct.c_double))
+            rep.history_cap = history
+        d = deflation.handle if deflation is not None else None
+        code = _lib().gmres_solve(self._h, d, ct.byref(opts), _ptr(b), _ptr(x), ct.byref(rep), _stream(stream))
+        if code not in (0, 5) or (code == 5 and raise_on_noconv):
+            raise DieError(code, "gmres_solve")
+        out = {"status": STATUS[code], "converged": code == 0, "cycles": rep.cycles, "iters": rep.iters,
+               "n_apply": rep.n_apply, "rel_res_solved": rep.rel_res_solved, "rel_res_orig": rep.rel_res_orig,
+               "t_matvec": rep.t_matvec, "t_orth": rep.t_orth, "t_defl": rep.t_defl, "t_total": rep.t_total}
+        if hist is not None:
+            out["history"] = hist[:rep.history_len].copy()
+        return x, out
+
+
+class Deflation:
+    """P^-1 = I + V (T^-1 - I) V^* for the r largest-magnitude eigenvalues (Eq. (4.12))."""
+
+    def __init__(self, op: Operator, r: int, tol: float = 1e-4, regularized: bool = True,
+                 inner: int = DIE_FP64, krylov_dim: int = 0, max_restarts: int = 0, seed: int = 0,
+                 r_max: int = 0, stream=None, allow_noconv: bool = True):
+        self.op = op
+        opts = DeflOpts(r, r_max, tol, int(bool(regularized)), inner, krylov_dim, max_restarts, seed)
+        cap = max(r, r_max, 64)
+        eig = (ct.c_double * (2 * cap))()
+        rout = ct.c_int(0)
+        h = ct.c_void_p()
+        code = _lib().deflation_build(op.handle, ct.byref(opts), _stream(stream), ct.byref(h), eig, ct.byref(rout))
+        if code != 0 and not (code == 5 and allow_noconv and h.value):
+            raise DieError(code, "deflation_build")
+        self._h = h
+        self.converged = code == 0
+        self.r = rout.value
+        import numpy as np
+        e = np.array(eig[:2 * self.r]).reshape(-1, 2)
+        self.eigenvalues = e[:, 0] + 1j * e[:, 1]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def apply(self, x, z=None, stream=None):
+        import torch
+        z = torch.empty_like(x) if z is None else z
+        _check(_lib().deflation_apply(self._h, _ptr(x), _ptr(z), _stream(stream)), "deflation_apply")
+        return z
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().deflation_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

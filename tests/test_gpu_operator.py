@@ -1,0 +1,134 @@
+"""GPU parity of the FFT-speed products with the CPU oracle (through the C ABI).
+
+Tolerances: FP64 products within 1e-10 relative (the FP64 gate); complex64 products
+within 2e-5 relative: single-precision rounding (6e-8) grows like the number of
+radix stages and the Green-spectrum dynamic range over two FFT passes per direction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dense, fftmv, rows  # noqa: E402
+from paper_1104_4263_gb300 import die, workloads as W  # noqa: E402
+
+FP64_TOL = 1e-10
+C64_TOL = 2e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+# grids: tiny, ragged (odd, non-square), a 3*2^a FFT size (n=33 -> M=96 is 3*32), n=61
+CASES = [(2, 2), (5, 3), (16, 16), (12, 7), (33, 20), (24, 33), (61, 9)]
+
+
+@pytest.mark.parametrize("n1,n2", CASES)
+def test_apply_matches_dense(n1, n2):
+    rng = W.rng_for(100, n1 * 1000 + n2)
+    eps = W.random_field(rng, n1, n2, -4.0, 16.0)
+    h = 0.8 / max(n1, n2)
+    x = W.random_vector(rng, n1, n2)
+    A = dense.dense_A(eps, h)
+    AR = dense.dense_AR(eps, h)
+    op = die.Operator(eps, h)
+    xt = dev(x)
+    assert rel(op.apply(xt).cpu().numpy(), dense.matvec(A, x)) < FP64_TOL
+    assert rel(op.apply_regularized(xt).cpu().numpy(), dense.matvec(AR @ A, x)) < FP64_TOL
+    assert rel(op.apply_regularizer(xt).cpu().numpy(), dense.matvec(AR, x)) < FP64_TOL
+    op32 = die.Operator(eps, h, prec=die.DIE_FP32_INNER)
+    x32 = dev(x, torch.complex64)
+    assert rel(op32.apply(x32).cpu().numpy(), dense.matvec(A, x)) < C64_TOL
+    assert rel(op32.apply_regularized(x32).cpu().numpy(), dense.matvec(AR @ A, x)) < C64_TOL
+
+
+@pytest.mark.parametrize("n1,n2,M", [(40, 40, (96, 96)), (40, 40, (96, 128)), (50, 30, (192, 64))])
+def test_apply_explicit_fft_sizes(n1, n2, M):
+    rng = W.rng_for(101, n1 + n2)
+    eps = W.random_field(rng, n1, n2)
+    h = 0.02
+    x = W.random_vector(rng, n1, n2)
+    ref = fftmv.FFTOperator(eps, h)
+    op = die.Operator(eps, h, M1=M[0], M2=M[1])
+    assert (op.M1, op.M2) == M
+    xt = dev(x)
+    assert rel(op.apply(xt).cpu().numpy(), ref.apply(x)) < FP64_TOL
+    assert rel(op.apply_regularized(xt).cpu().numpy(), ref.apply_regularized(x)) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [64, 96, 128, 200])
+def test_apply_matches_fft_oracle(n):
+    p = W.core_shell(n, side=n / 64.0, r_core=1.5 * n / 512, r_shell=2.5 * n / 512)
+    rng = W.rng_for(102, n)
+    x = W.random_vector(rng, n, n)
+    ref = fftmv.FFTOperator(p.eps_r, p.h)
+    op = die.Operator(p.eps_r, p.h)
+    xt = dev(x)
+    assert rel(op.apply(xt).cpu().numpy(), ref.apply(x)) < FP64_TOL
+    assert rel(op.apply_regularized(xt).cpu().numpy(), ref.apply_regularized(x)) < FP64_TOL
+    op32 = die.Operator(p.eps_r, p.h, prec=die.DIE_FP32_INNER)
+    assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), ref.apply_regularized(x)) < C64_TOL
+
+
+def test_in_place_apply():
+    p = W.config1(16)
+    rng = W.rng_for(103)
+    x = W.random_vector(rng, 16, 16)
+    op = die.Operator(p.eps_r, p.h)
+    xt = dev(x)
+    ref = op.apply_regularized(xt).clone()
+    op.apply_regularized(xt, xt)
+    assert torch.equal(xt, ref)
+
+
+def test_plane_wave_matches_oracle():
+    op = die.Operator(np.ones((9, 13), dtype=complex), 0.07)
+    for psi in (0.0, 0.3, 2.0, -1.0):
+        b = op.plane_wave(psi).cpu().numpy()
+        assert np.max(np.abs(b - dense.plane_wave(13, 9, 0.07, psi))) < 1e-12
+
+
+def test_full_size_core_shell_512():
+    """512^2 core-shell workload: the whole product against the (pinned) CPU FFT oracle,
+    and 64 seeded rows against exact dense sums."""
+    p = W.config2(512)
+    rng = W.rng_for(104)
+    x = W.random_vector(rng, 512, 512)
+    op = die.Operator(p.eps_r, p.h)
+    y = op.apply(dev(x)).cpu().numpy()
+    ref = fftmv.FFTOperator(p.eps_r, p.h, workers=8)
+    assert rel(y, ref.apply(x)) < FP64_TOL
+    idx = rng.choice(2 * 512 * 512, size=64, replace=False)
+    got = y.reshape(-1)[idx]
+    exact = rows.rows_apply(dense.contrast(p.eps_r), x, p.h, idx)
+    assert np.max(np.abs(got - exact)) / np.max(np.abs(y)) < FP64_TOL
+    yr = op.apply_regularized(dev(x)).cpu().numpy()
+    assert rel(yr, ref.apply_regularized(x)) < FP64_TOL
+
+
+def test_singular_permittivity_rejected():
+    eps = np.full((8, 8), 4.0 + 0j)
+    eps[3, 5] = 0.0
+    with pytest.raises(die.DieError) as e:
+        die.Operator(eps, 0.1)
+    assert e.value.code == 4
+    eps[3, 5] = np.nan
+    with pytest.raises(die.DieError):
+        die.Operator(eps, 0.1)
+
+
+def test_eps_on_device_matches_host():
+    p = W.config1(20)
+    rng = W.rng_for(105)
+    x = dev(W.random_vector(rng, 20, 20))
+    a = die.Operator(p.eps_r, p.h).apply(x)
+    b = die.Operator(torch.from_numpy(p.eps_r).cuda(), p.h).apply(x)
+    assert torch.equal(a, b)

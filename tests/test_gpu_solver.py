@@ -1,0 +1,166 @@
+"""GPU restarted GMRES and deflation against the CPU oracle (through the C ABI)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import cylinder, deflation, dense, gmres  # noqa: E402
+from paper_1104_4263_gb300 import die, workloads as W  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def cyl32():
+    p = W.config1(32)
+    A = dense.dense_A(p.eps_r, p.h)
+    b = dense.plane_wave(32, 32, p.h, 0.0)
+    x = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
+    return p, A, b, x
+
+
+def test_plain_gmres_config1(cyl32):
+    """Cylinder eps 4, 32^2, GMRES(20) to 1e-8 (FP64): same solution and about the same
+    number of steps as the oracle's GMRES(20)."""
+    p, A, b, x = cyl32
+    op = die.Operator(p.eps_r, p.h)
+    bt = op.plane_wave(0.0)
+    assert np.max(np.abs(bt.cpu().numpy() - b)) < 1e-12
+    u, rep = op.solve(bt, restart=20, tol=1e-8, max_iters=20000, history=5000)
+    assert rep["converged"] and rep["rel_res_solved"] <= 1e-8
+    kappa = np.linalg.cond(A)
+    assert rel(u.cpu().numpy(), x) < 10 * kappa * 1e-8
+    ref = gmres.gmres(lambda v: dense.matvec(A, v), b, 20, 1e-8, 20000)
+    h = rep["history"]
+    assert len(h) == rep["iters"] and h[-1] <= 1e-8 * 1.01
+    # first cycle: the same Krylov space in exact arithmetic -> estimates agree to rounding
+    first = np.array(ref.history[:20])
+    assert np.max(np.abs(h[:20] - first) / first) < 1e-9
+    # later cycles drift by rounding (CGS2 here, MGS in the oracle); totals stay close
+    assert abs(rep["iters"] - ref.iters) <= 0.1 * ref.iters, (rep["iters"], ref.iters)
+
+
+def test_field_matches_cylinder_series(cyl32):
+    p, A, b, x = cyl32
+    op = die.Operator(p.eps_r, p.h)
+    u, rep = op.solve(op.plane_wave(0.0), restart=20, tol=1e-10, max_iters=20000)
+    X1, X2 = W.mesh(32, 32, p.h)
+    E1, E2, _ = cylinder.field(4.0, 1.0, X1, X2, 0.0)
+    err = rel(u.cpu().numpy(), np.stack([E1, E2]))
+    assert err < 0.35
+
+
+def test_mixed_precision_and_regularized(cyl32):
+    p, A, b, x = cyl32
+    op = die.Operator(p.eps_r, p.h)
+    bt = op.plane_wave(0.0)
+    for reg in (False, True):
+        u, rep = op.solve(bt, restart=20, tol=1e-8, max_iters=20000, regularized=reg, inner=die.DIE_FP32_INNER)
+        assert rep["converged"] and rep["rel_res_solved"] <= 1e-8
+        assert rel(u.cpu().numpy(), x) < 1e-5
+        u2, rep2 = op.solve(bt, restart=20, tol=1e-8, max_iters=20000, regularized=reg)
+        assert rep2["converged"] and rel(u2.cpu().numpy(), x) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def small_core_shell():
+    n = 12
+    eps = W.core_shell(n, side=1.2, r_core=0.25, r_shell=0.5, eps_core=-2 + 0.1j, eps_shell=20 + 0.5j).eps_r
+    h = 0.1
+    A = dense.dense_A(eps, h)
+    AR = dense.dense_AR(eps, h)
+    b = dense.plane_wave(n, n, h, 0.0)
+    x = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
+    return eps, h, A, AR, b, x
+
+
+def test_deflation_eigenvalues_match_dense(small_core_shell):
+    eps, h, A, AR, b, x = small_core_shell
+    op = die.Operator(eps, h)
+    r = R_DEFL
+    D = die.Deflation(op, r, tol=1e-8, regularized=True)
+    assert D.converged and D.r == r
+    ref = np.linalg.eigvals(AR @ A)
+    ref = ref[np.argsort(-np.abs(ref), kind="stable")][:r]
+    got = D.eigenvalues
+    for z in ref:
+        assert np.min(np.abs(got - z)) < 1e-6 * abs(z)
+
+
+def test_deflated_directions_map_to_one(small_core_shell):
+    """For v in span(V): Atilde P^-1 v = v (Eq. (4.12) with T = V^* Atilde V)."""
+    eps, h, A, AR, b, x = small_core_shell
+    op = die.Operator(eps, h)
+    D = die.Deflation(op, R_DEFL, tol=1e-10, regularized=True)
+    rng = W.rng_for(110)
+    xx = torch.from_numpy(W.random_vector(rng, 12, 12)).cuda()
+    u = D.apply(xx) - xx                     # in span(V)
+    lhs = op.apply_regularized(D.apply(u))
+    assert rel(lhs.cpu().numpy(), u.cpu().numpy()) < 1e-8
+
+
+# r = 11 keeps the 10th/11th eigenvalues (an exactly degenerate pair of this symmetric
+# object) together, so the deflated subspace is well defined.
+R_DEFL = 11
+
+
+def test_deflation_apply_matches_oracle(small_core_shell):
+    eps, h, A, AR, b, x = small_core_shell
+    op = die.Operator(eps, h)
+    D = die.Deflation(op, R_DEFL, tol=1e-10, regularized=True)
+    ref = deflation.Deflation(AR @ A, R_DEFL)
+    rng = W.rng_for(111)
+    xx = W.random_vector(rng, 12, 12)
+    z = D.apply(torch.from_numpy(xx).cuda()).cpu().numpy()
+    assert rel(z, ref.apply(xx)) < 1e-7
+
+
+def test_regularized_deflated_solve(small_core_shell):
+    """A_R A P^-1 v = A_R b converges where plain GMRES(60) stalls, to the direct solution."""
+    eps, h, A, AR, b, x = small_core_shell
+    op = die.Operator(eps, h)
+    bt = torch.from_numpy(b).cuda()
+    D = die.Deflation(op, R_DEFL, tol=1e-6, regularized=True)
+    assert D.converged
+    kappa = np.linalg.cond(A)
+    for inner in (die.DIE_FP64, die.DIE_FP32_INNER):
+        u, rep = op.solve(bt, restart=60, tol=1e-8, max_iters=3000, regularized=True, deflation=D, inner=inner)
+        assert rep["converged"], (inner, rep)
+        assert rel(u.cpu().numpy(), x) < 10 * kappa * 1e-8
+        assert rep["rel_res_orig"] < 1e-6
+    _, rep = op.solve(bt, restart=60, tol=1e-8, max_iters=1500)
+    assert not rep["converged"]
+
+
+def test_status_codes():
+    p = W.config1(16)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    _, rep = op.solve(b, restart=5, tol=1e-12, max_iters=3)
+    assert rep["status"] == "DIE_ENOCONV" and rep["iters"] == 3
+    bad = b.clone()
+    bad[0, 3, 3] = float("nan")
+    with pytest.raises(die.DieError) as e:
+        op.solve(bad, restart=5, tol=1e-8, max_iters=10)
+    assert e.value.code == 7
+    with pytest.raises(die.DieError) as e:
+        op.solve(b, restart=0, tol=1e-8, max_iters=10)
+    assert e.value.code == 1
+    z, rep = op.solve(torch.zeros_like(b), restart=5, tol=1e-8, max_iters=10)
+    assert rep["converged"] and float(z.abs().max()) == 0.0
+
+
+def test_deflation_for_other_operator_rejected():
+    p = W.config1(12)
+    op1 = die.Operator(p.eps_r, p.h)
+    op2 = die.Operator(p.eps_r, p.h)
+    D = die.Deflation(op1, 4, regularized=True)
+    with pytest.raises(die.DieError):
+        op2.solve(op2.plane_wave(0.0), regularized=True, deflation=D, max_iters=10)
+    with pytest.raises(die.DieError):
+        op1.solve(op1.plane_wave(0.0), regularized=False, deflation=D, max_iters=10)
