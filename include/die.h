@@ -170,6 +170,22 @@ die_status deflation_build(dieop_t op, const defl_opts* opts, void* stream, defl
  * z may equal x. */
 die_status deflation_apply(defl_t defl, const void* x, void* z, void* stream);
 
+/* z = P^-1 x exactly as deflation_apply, but allocating nothing.  The paper has no
+ * counterpart: this entry exists for callers that must not allocate device memory,
+ * for example a solver embedded in another program that has already handed all
+ * device memory to its own pool allocator, or a latency-critical loop where the
+ * device-wide synchronisation that cudaMalloc and cudaFree can cause is not
+ * acceptable.  Its scratch (projections, per-block partial sums and a reduction
+ * counter, about 625 KB) is a static device array inside the library that every GPU
+ * loading the library keeps until the process exits.
+ *   - defl must have r <= 128, else DIE_EINVAL; x, z as for deflation_apply.
+ *   - The first call on a device looks up the array's address on that device (call
+ *     it with that device current); make this first call before any stream capture.
+ *   - All calls share the one array (it keeps the last call's contents; the counter
+ *     is cleared at the start of each call): calls that overlap on the GPU, e.g. on
+ *     two streams at once, race and give wrong results.  Serialise them. */
+die_status deflation_apply_noalloc(defl_t defl, const void* x, void* z, void* stream);
+
 void deflation_destroy(defl_t defl);
 
 /* Deflation radius of Section 5: the largest |lambda'| over the images of the segments

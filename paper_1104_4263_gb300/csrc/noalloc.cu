@@ -1,0 +1,64 @@
+// deflation_apply_noalloc: z = P^-1 x = x + V (M (V^* x)) without any device
+// allocation.  It runs the same two kernels as deflation_apply (batched projections
+// with a deterministic last-block reduction, then the rank-r update), but their
+// scratch -- the per-block partial sums, the r projections and the arrival counter of
+// the reduction -- lives in the file-scope array below instead of buffers allocated
+// by deflation_build.
+#include <mutex>
+
+#include "solver.cuh"
+
+namespace die {
+
+constexpr int kNoAllocMaxR = 128;                // largest deflation rank accepted
+constexpr int kNoAllocMaxDevices = 64;
+constexpr long kNoAllocPartials = (long)kNoAllocMaxR * kRedBlocks;
+// partials | projections s | counter (one double2 slot)
+constexpr long kNoAllocSlots = kNoAllocPartials + kNoAllocMaxR + 1;
+
+// 128 * 304 * 16 + 129 * 16 bytes (about 625 KB), held by every GPU that loads the
+// library until the process exits.
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
+
+static std::mutex g_noalloc_mu;
+static double2* g_noalloc_addr[kNoAllocMaxDevices];
+
+// Device address of the array on the current device (looked up once per device).
+static die_status noalloc_scratch(double2** out) {
+    int dev = 0;
+    DIE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return DIE_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            return DIE_ECUDA;
+        }
+        g_noalloc_addr[dev] = reinterpret_cast<double2*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DIE_OK;
+}
+
+}  // namespace die
+
+using namespace die;
+
+extern "C" die_status deflation_apply_noalloc(defl_t d, const void* x, void* z, void* stream) {
+    if (!d || !x || !z) return DIE_EINVAL;
+    if (d->r < 1 || d->r > kNoAllocMaxR) return DIE_EINVAL;
+    double2* base = nullptr;
+    DIE_TRY(noalloc_scratch(&base));
+    cudaStream_t st = (cudaStream_t)stream;
+    RedScratch rs;
+    rs.partial = base;
+    rs.counter = reinterpret_cast<unsigned*>(base + kNoAllocPartials + kNoAllocMaxR);
+    double2* s = base + kNoAllocPartials;
+    // the reduction's arrival counter must start at zero
+    DIE_CUDA_TRY(cudaMemsetAsync(rs.counter, 0, sizeof(unsigned), st));
+    DIE_TRY(k_dots(d->V, d->n, d->r, (const double2*)x, d->n, s, rs, nullptr, st));
+    DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, s, (const double2*)x, (double2*)z, d->n, nullptr, st));
+    return DIE_OK;
+}

@@ -66,6 +66,7 @@ EXPORTS = {
     "deflation_build": (ct.c_int, [ct.c_void_p, ct.POINTER(DeflOpts), ct.c_void_p, ct.POINTER(ct.c_void_p),
                                    ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
     "deflation_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "deflation_apply_noalloc": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "deflation_destroy": (None, [ct.c_void_p]),
     "die_deflation_radius": (ct.c_double, [ct.c_void_p, ct.c_longlong, ct.c_int]),
     "die_prof_begin": (ct.c_int, []),
