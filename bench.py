@@ -267,6 +267,7 @@ def main():
     launches = sum(v["launches"] for v in kt.result.values())
     out["gpu_launches"] = launches
     out["gmres"] = {"solve_s": solve_s, "iters": reps[-1]["iters"], "cycles": reps[-1]["cycles"],
+                    "n_reorth": reps[-1]["n_reorth"],
                     "rel_res_solved": reps[-1]["rel_res_solved"], "rel_res_orig": reps[-1]["rel_res_orig"],
                     "status": reps[-1]["status"], "deflation_build_s": t_defl, "operator_setup_s": t_setup,
                     "deflation_converged": D.converged}

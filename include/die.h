@@ -108,8 +108,11 @@ void dieop_destroy(dieop_t op);
  * Solves Atilde x = btilde with Atilde = A (regularized = 0) or A_R A and
  * btilde = A_R b (regularized = 1), right-preconditioned by the deflation
  * P^-1 of Eq. (4.12) when a defl_t is given: Atilde P^-1 v = btilde, x = P^-1 v.
- * Arnoldi by CGS2 (classical Gram-Schmidt with one re-orthogonalisation), FP64;
- * Hessenberg least squares by Givens rotations, FP64, on the device.
+ * Arnoldi by classical Gram-Schmidt with the DGKS criterion (a second pass when
+ * the first removed more than half of ||w||^2), FP64; Hessenberg least squares by
+ * Givens rotations, FP64, on the device.  With inner = DIE_FP32_INNER the products
+ * with Atilde inside a cycle and the deflation P^-1 run in complex64 (a fixed
+ * preconditioner for the whole solve); the restart residual stays FP64.
  * ------------------------------------------------------------------------- */
 typedef struct gmres_opts {
     int restart;           /* Krylov dimension per cycle, 1..256                               */
@@ -120,6 +123,10 @@ typedef struct gmres_opts {
     die_precision inner;   /* DIE_FP64, or DIE_FP32_INNER: complex64 products inside a cycle,
                               FP64 restart residual (iterative refinement)                      */
     int timing;            /* 1: fill t_matvec/t_orth/t_defl (adds stream syncs)               */
+    double reorth_eta;     /* DGKS threshold: second Gram-Schmidt pass when ||w'|| < eta ||w||;
+                              <= 0 selects 0.01 (one CGS pass loses about eps ||w||/||w'|| of
+                              orthogonality: <= 2.3e-14 at 0.01); 1/sqrt(2) is the classical
+                              choice; >= 1 always re-orthogonalises                             */
 } gmres_opts;
 
 typedef struct gmres_report {
@@ -132,6 +139,7 @@ typedef struct gmres_report {
     double* history;       /* caller-owned host buffer for per-step residual estimates, or NULL */
     int history_cap;       /* its length                                                       */
     int history_len;       /* entries written                                                  */
+    int n_reorth;          /* Arnoldi steps that needed the second Gram-Schmidt pass           */
 } gmres_report;
 
 /* b, x: device complex128, 2*n1*n2.  defl may be NULL.  report may be NULL.

@@ -1,43 +1,27 @@
-// Krylov-space kernels (see krylov.cuh).  Reductions: every block accumulates a
-// fixed, grid-strided share of the rows, reduces it with warp shuffles in a fixed
-// order and writes one partial per vector; the last block to arrive (atomic
-// counter) sums the partials of each vector in a fixed order.  Results therefore
-// do not depend on scheduling.
+// Krylov-space kernels (see krylov.cuh).
+//
+// Projections: each block owns a contiguous slice of the rows; each warp accumulates
+// whole vectors over that slice (lanes stride the rows, so basis reads are coalesced,
+// w is re-read from L1, and there is no barrier or reduction until the end), then one
+// warp reduction per vector gives the block's partial.  The last block to arrive
+// (atomic counter) sums the partials of each vector in a fixed order, so results do
+// not depend on scheduling.  Updates: one thread per row, sum over the basis with
+// fused multiply-adds (4 per complex term); the optional norm uses the same
+// deterministic two-level reduction.  Every complex multiply-add is written as four
+// FMAs: on GB300 the FP64 pipe (about 2 FMA per clock per SM) bounds these kernels.
 #include "krylov.cuh"
 #include "prof.cuh"
 
 namespace die {
 
-__device__ __forceinline__ double2 shfl_down2(double2 v, int off) {
-    v.x = __shfl_down_sync(0xffffffffu, v.x, off);
-    v.y = __shfl_down_sync(0xffffffffu, v.y, off);
-    return v;
-}
+template <typename V> struct acc_of;
+template <> struct acc_of<double2> { using type = double; };
+template <> struct acc_of<float2> { using type = float; };
 
-__device__ __forceinline__ double2 warp_sum(double2 v) {
+__device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) { double2 o = shfl_down2(v, off); v.x += o.x; v.y += o.y; }
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     return v;
-}
-
-// Reduce acc[0..cnt) over the block and store the block's partials of vectors vbase + i.
-template <int CH>
-__device__ __forceinline__ void block_partials(double2 (&acc)[CH], int cnt, double2* partial, int vbase) {
-    __shared__ double2 red[kRedThreads / 32][CH];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < CH; i++) acc[i] = warp_sum(acc[i]);
-    if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < CH; i++) red[warp][i] = acc[i];
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-        double2 s = make_double2(0, 0);
-        for (int w = 0; w < kRedThreads / 32; w++) { s.x += red[w][threadIdx.x].x; s.y += red[w][threadIdx.x].y; }
-        partial[(long)(vbase + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
-    }
-    __syncthreads();
 }
 
 // True in exactly one block: the last one to finish writing its partials.
@@ -55,115 +39,231 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter) {
 __device__ __forceinline__ void final_sums(const double2* partial, int nv, double2* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < nv; i += nw) {
-        double2 s = make_double2(0, 0);
+        double sx = 0, sy = 0;
         for (int b = lane; b < (int)gridDim.x; b += 32) {
             const double2 p = __ldcg(&partial[(long)i * kRedBlocks + b]);
-            s.x += p.x; s.y += p.y;
+            sx += p.x;
+            sy += p.y;
         }
-        s = warp_sum(s);
-        if (lane == 0) out[i] = s;
+        sx = warp_sum_d(sx);
+        sy = warp_sum_d(sy);
+        if (lane == 0) out[i] = make_double2(sx, sy);
     }
 }
 
-constexpr int kCh = 8;
+// Rows loaded per batch by each lane: enough independent loads in flight to cover
+// HBM latency with two blocks of eight warps per SM.
+template <typename VT> constexpr int dot_batch() { return sizeof(VT) == 8 ? 8 : 4; }
 
-// acc_i += conj(V_i[idx]) w[idx] for vectors c0 .. c0+cnt over this thread's rows.
-__device__ __forceinline__ void dot_chunk(const double2* __restrict__ V, long ldv, int c0, int cnt,
-                                          const double2* __restrict__ w, long n, double2 (&acc)[kCh]) {
+// out[i] = sum_e conj(V_i[e]) w[e]; w has the basis' element type (no conversions).
+// Warp q of a block handles vectors q, q+8, q+16, ... one at a time over the block's rows.
+template <typename VT>
+__global__ void __launch_bounds__(kRedThreads) dots_kernel(const VT* __restrict__ V, long ldv, int nv,
+                                                           const VT* __restrict__ w, long n, int with_norm,
+                                                           double2* out, RedScratch rs, const int* skip) {
+    using A = typename acc_of<VT>::type;
+    constexpr int U = dot_batch<VT>();
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long r0 = n * (long)blockIdx.x / gridDim.x, r1 = n * (long)(blockIdx.x + 1) / gridDim.x;
+    const int nvt = nv + (with_norm ? 1 : 0);
+    for (int i = warp; i < nvt; i += 8) {
+        A ax = 0, ay = 0, bx = 0, by = 0;
+        long idx = r0 + lane;
+        if (i < nv) {
+            const VT* p = V + (long)i * ldv;
+            for (; idx + 32 * (U - 1) < r1; idx += 32 * U) {
+                VT a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) { a[u] = p[idx + 32 * u]; b[u] = w[idx + 32 * u]; }
+#pragma unroll
+                for (int u = 0; u < U; u += 2) {
+                    ax = fma(a[u].x, b[u].x, ax); ax = fma(a[u].y, b[u].y, ax);
+                    ay = fma(a[u].x, b[u].y, ay); ay = fma(-a[u].y, b[u].x, ay);
+                    bx = fma(a[u + 1].x, b[u + 1].x, bx); bx = fma(a[u + 1].y, b[u + 1].y, bx);
+                    by = fma(a[u + 1].x, b[u + 1].y, by); by = fma(-a[u + 1].y, b[u + 1].x, by);
+                }
+            }
+            for (; idx < r1; idx += 32) {
+                const VT a = p[idx], b = w[idx];
+                ax = fma(a.x, b.x, ax); ax = fma(a.y, b.y, ax);
+                ay = fma(a.x, b.y, ay); ay = fma(-a.y, b.x, ay);
+            }
+        } else {                                            // the norm of w
+            for (; idx + 32 * (U - 1) < r1; idx += 32 * U) {
+                VT b[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) b[u] = w[idx + 32 * u];
+#pragma unroll
+                for (int u = 0; u < U; u++) { ax = fma(b[u].x, b[u].x, ax); bx = fma(b[u].y, b[u].y, bx); }
+            }
+            for (; idx < r1; idx += 32) {
+                const VT b = w[idx];
+                ax = fma(b.x, b.x, ax);
+                bx = fma(b.y, b.y, bx);
+            }
+            ax += bx;
+            bx = 0;
+        }
+        const double sx = warp_sum_d((double)ax + (double)bx), sy = warp_sum_d((double)ay + (double)by);
+        if (lane == 0) rs.partial[(long)i * kRedBlocks + blockIdx.x] = make_double2(sx, sy);
+    }
+    if (arrive_last(rs.counter)) {
+        final_sums(rs.partial, nvt, out);
+        if (threadIdx.x == 0) *rs.counter = 0;
+    }
+}
+
+// z = x + V c with c = M s (rounded to FP32), all complex64: the deflation update of
+// the FP32-inner solves.  Each block forms c redundantly.
+__global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2* __restrict__ V, long ldv, int r,
+                                                                    const double2* __restrict__ M,
+                                                                    const double2* __restrict__ s,
+                                                                    const float2* x, float2* z, long n,
+                                                                    const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float2 cs[kMaxBasis];
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        double cx = 0, cy = 0;
+        for (int q = 0; q < r; q++) {
+            const double2 m = M[(long)q * r + i], sv = s[q];
+            cx = fma(m.x, sv.x, cx); cx = fma(-m.y, sv.y, cx);
+            cy = fma(m.x, sv.y, cy); cy = fma(m.y, sv.x, cy);
+        }
+        cs[i] = make_float2((float)cx, (float)cy);
+    }
+    __syncthreads();
     const long stride = (long)gridDim.x * blockDim.x;
-#pragma unroll
-    for (int i = 0; i < kCh; i++) acc[i] = make_double2(0, 0);
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const double2 wv = w[idx];
-#pragma unroll
-        for (int i = 0; i < kCh; i++) {
-            if (i < cnt) {
-                const double2 a = V[(long)(c0 + i) * ldv + idx];
-                acc[i].x = fma(a.x, wv.x, fma(a.y, wv.y, acc[i].x));
-                acc[i].y = fma(a.x, wv.y, fma(-a.y, wv.x, acc[i].y));
+        float2 acc = x[idx];
+        float ex = 0, ey = 0;
+        int i = 0;
+#pragma unroll 4
+        for (; i + 1 < r; i += 2) {
+            const float2 a = V[(long)i * ldv + idx], c = cs[i];
+            const float2 b = V[(long)(i + 1) * ldv + idx], d = cs[i + 1];
+            acc.x = fmaf(a.x, c.x, acc.x); acc.x = fmaf(-a.y, c.y, acc.x);
+            acc.y = fmaf(a.x, c.y, acc.y); acc.y = fmaf(a.y, c.x, acc.y);
+            ex = fmaf(b.x, d.x, ex); ex = fmaf(-b.y, d.y, ex);
+            ey = fmaf(b.x, d.y, ey); ey = fmaf(b.y, d.x, ey);
+        }
+        if (i < r) {
+            const float2 a = V[(long)i * ldv + idx], c = cs[i];
+            acc.x = fmaf(a.x, c.x, acc.x); acc.x = fmaf(-a.y, c.y, acc.x);
+            acc.y = fmaf(a.x, c.y, acc.y); acc.y = fmaf(a.y, c.x, acc.y);
+        }
+        z[idx] = make_float2(acc.x + ex, acc.y + ey);
+    }
+}
+
+// out = base + sum_i V_i c_i.  Coefficients: c = sign * coef, or c = M s when M != NULL.
+template <typename VT, bool NORM>
+__global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __restrict__ V, long ldv, int k,
+                                                                 const double2* __restrict__ coef, double sign,
+                                                                 const double2* __restrict__ M,
+                                                                 const double2* __restrict__ s, const double2* base,
+                                                                 double2* out, long n, double2* nrm2, Dgks dec,
+                                                                 int has_dec, RedScratch rs, const int* skip) {
+    using A = typename acc_of<VT>::type;
+    if (skip && *skip) return;
+    __shared__ VT cs[kMaxBasis];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double cx = 0, cy = 0;
+        if (M) {
+            for (int q = 0; q < k; q++) {
+                const double2 m = M[(long)q * k + i], sv = s[q];
+                cx = fma(m.x, sv.x, cx); cx = fma(-m.y, sv.y, cx);
+                cy = fma(m.x, sv.y, cy); cy = fma(m.y, sv.x, cy);
+            }
+        } else {
+            cx = sign * coef[i].x;
+            cy = sign * coef[i].y;
+        }
+        VT c;
+        c.x = (A)cx;
+        c.y = (A)cy;
+        cs[i] = c;
+    }
+    __syncthreads();
+    double nacc = 0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        A x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        int i = 0;
+#pragma unroll 4
+        for (; i + 1 < k; i += 2) {
+            const VT a = V[(long)i * ldv + idx], c = cs[i];
+            const VT b = V[(long)(i + 1) * ldv + idx], d = cs[i + 1];
+            x0 = fma(a.x, c.x, x0); x0 = fma(-a.y, c.y, x0);
+            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+            x1 = fma(b.x, d.x, x1); x1 = fma(-b.y, d.y, x1);
+            y1 = fma(b.x, d.y, y1); y1 = fma(b.y, d.x, y1);
+        }
+        if (i < k) {
+            const VT a = V[(long)i * ldv + idx], c = cs[i];
+            x0 = fma(a.x, c.x, x0); x0 = fma(-a.y, c.y, x0);
+            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+        }
+        double2 o = make_double2((double)x0 + (double)x1, (double)y0 + (double)y1);
+        if (base) { const double2 bv = base[idx]; o.x += bv.x; o.y += bv.y; }
+        out[idx] = o;
+        if (NORM) { nacc = fma(o.x, o.x, nacc); nacc = fma(o.y, o.y, nacc); }
+    }
+    if (NORM) {
+        __shared__ double red[kRedThreads / 32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        nacc = warp_sum_d(nacc);
+        if (lane == 0) red[warp] = nacc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int q = 0; q < kRedThreads / 32; q++) t += red[q];
+            rs.partial[blockIdx.x] = make_double2(t, 0.0);
+        }
+        if (arrive_last(rs.counter)) {
+            __shared__ double2 tot;
+            final_sums(rs.partial, 1, &tot);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                *rs.counter = 0;
+                *nrm2 = tot;
+                if (has_dec) {
+                    const int r = dec.always || tot.x < dec.eta2 * dec.before2->x;
+                    *dec.reorth = r;
+                    *dec.skip2 = (dec.done && *dec.done) || !r;
+                }
             }
         }
     }
 }
 
-__device__ __forceinline__ void all_dots(const double2* V, long ldv, int nv, const double2* w, long n, double2* partial) {
-    for (int c0 = 0; c0 < nv; c0 += kCh) {
-        const int cnt = imin(kCh, nv - c0);
-        double2 acc[kCh];
-        dot_chunk(V, ldv, c0, cnt, w, n, acc);
-        block_partials<kCh>(acc, cnt, partial, c0);
-    }
-}
-
-// w[idx] -= sum_i V_i[idx] h_i over this thread's rows (h in shared memory).
-__device__ __forceinline__ void update_rows(const double2* __restrict__ V, long ldv, int nv, double2* __restrict__ w,
-                                            long n, const double2* hs) {
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        double2 wv = w[idx];
-        for (int i = 0; i < nv; i++) {
-            const double2 a = V[(long)i * ldv + idx];
-            const double2 hh = hs[i];
-            wv.x -= a.x * hh.x - a.y * hh.y;
-            wv.y -= a.x * hh.y + a.y * hh.x;
-        }
-        w[idx] = wv;
-    }
-}
-
-__global__ void __launch_bounds__(kRedThreads) dots_kernel(const double2* V, long ldv, int nv, const double2* w,
-                                                           long n, double2* out, RedScratch rs, const int* skip) {
-    if (skip && *skip) return;
-    all_dots(V, ldv, nv, w, n, rs.partial);
-    if (arrive_last(rs.counter)) {
-        final_sums(rs.partial, nv, out);
-        if (threadIdx.x == 0) *rs.counter = 0;
-    }
-}
-
-__global__ void __launch_bounds__(kRedThreads) update_dots_kernel(const double2* V, long ldv, int nv, double2* w,
-                                                                  long n, const double2* h, double2* out,
-                                                                  RedScratch rs, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ double2 hs[kMaxBasis];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
-    __syncthreads();
-    update_rows(V, ldv, nv, w, n, hs);
-    all_dots(V, ldv, nv, w, n, rs.partial);   // each thread re-reads only rows it wrote
-    if (arrive_last(rs.counter)) {
-        final_sums(rs.partial, nv, out);
-        if (threadIdx.x == 0) *rs.counter = 0;
-    }
-}
-
-__global__ void __launch_bounds__(kRedThreads) update_norm_kernel(const double2* V, long ldv, int nv, double2* w,
-                                                                  long n, const double2* h, double2* out,
-                                                                  RedScratch rs, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ double2 hs[kMaxBasis];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
-    __syncthreads();
-    update_rows(V, ldv, nv, w, n, hs);
-    all_dots(w, 0, 1, w, n, rs.partial);
-    if (arrive_last(rs.counter)) {
-        final_sums(rs.partial, 1, out);
-        if (threadIdx.x == 0) *rs.counter = 0;
-    }
-}
-
 // One Givens step of the restarted GMRES least-squares problem (Saad & Schultz):
-// H(:, j) = h1 + h2 with H(j+1, j) = ||w||; apply the stored rotations, build the
+// H(:, j) = h1 (+ h2) with H(j+1, j) = ||w||; apply the stored rotations, build the
 // rotation that annihilates H(j+1, j), update g; residual estimate |g_{j+1}| / ||b||.
-__device__ void givens_step(GmresDev S, int j, int step, double wnorm2, double wnorm2_before) {
+// The column, the stored rotations and g_j are staged in shared memory by the whole
+// block (one global round trip instead of one per rotation), then thread 0 computes.
+__global__ void arnoldi_finish_kernel(GmresDev S, int j, int step) {
+    __shared__ double2 col[kMaxBasis + 2], csv[kMaxBasis], snv[kMaxBasis];
+    if (*S.done) return;
     const int ld = S.m + 1;
-    double2* Hc = S.H + (long)j * ld;
-    for (int i = 0; i <= j; i++) Hc[i] = make_double2(S.h1[i].x + S.h2[i].x, S.h1[i].y + S.h2[i].y);
+    double2* Hgl = S.H + (long)j * ld;
+    const int re = *S.reorth;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        col[i] = re ? make_double2(S.h1[i].x + S.h2[i].x, S.h1[i].y + S.h2[i].y) : S.h1[i];
+        if (i < j) { csv[i] = S.cs[i]; snv[i] = S.sn[i]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+    double2* Hc = col;
+    if (re) *S.nreorth += 1;
+    const double wnorm2 = re ? S.nrm[1].x : S.nrm[0].x;
+    const double before2 = S.h1[j + 1].x;
     const double hn = sqrt(fmax(wnorm2, 0.0));
     *S.wnorm = hn;
     Hc[j + 1] = make_double2(hn, 0.0);
     for (int i = 0; i < j; i++) {
-        const double c = S.cs[i].x;
-        const double2 s = S.sn[i];
+        const double c = csv[i].x;
+        const double2 s = snv[i];
         const double2 a = Hc[i], b = Hc[i + 1];
         Hc[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
         // -conj(s) a + c b
@@ -191,52 +291,37 @@ __device__ void givens_step(GmresDev S, int j, int step, double wnorm2, double w
     if (step < S.hist_cap) S.hist[step] = est;
     *S.k = j + 1;
     const bool bad = !isfinite(est) || !isfinite(hn);
-    const bool breakdown = hn <= 1e-14 * sqrt(fmax(wnorm2_before, 0.0));
+    const bool breakdown = hn <= 1e-14 * sqrt(fmax(before2, 0.0));
     if (bad) *S.flags |= 1;
     if (breakdown) *S.flags |= 2;
     if (bad || breakdown || est <= S.tol || j + 1 >= S.jmax) *S.done = 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hgl[i] = col[i];
 }
 
-__global__ void __launch_bounds__(kRedThreads) update_norm_givens_kernel(const double2* V, long ldv, int nv,
-                                                                         double2* w, long n, GmresDev S, int j,
-                                                                         int step, RedScratch rs) {
-    if (*S.done) return;
-    __shared__ double2 hs[kMaxBasis];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = S.h2[i];
-    __syncthreads();
-    update_rows(V, ldv, nv, w, n, hs);
-    all_dots(w, 0, 1, w, n, rs.partial);
-    if (arrive_last(rs.counter)) {
-        __shared__ double2 nrm;
-        final_sums(rs.partial, 1, &nrm);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            *rs.counter = 0;
-            givens_step(S, j, step, nrm.x, S.h1[nv].x);
-        }
+// v *= inv, with an optional complex64 copy of the result
+__device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float2* v32) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 a = v[i];
+        const double2 b = make_double2(a.x * inv, a.y * inv);
+        v[i] = b;
+        if (v32) v32[i] = make_float2((float)b.x, (float)b.y);
     }
 }
 
-__global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip) {
+__global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32) {
     if (skip && *skip) return;
     const double s2 = nrm2->x;
     if (!(s2 > 0.0) || !isfinite(s2)) return;
-    const double inv = 1.0 / sqrt(s2);
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        double2 a = v[i];
-        v[i] = make_double2(a.x * inv, a.y * inv);
-    }
+    scale_rows(v, n, 1.0 / sqrt(s2), v32);
 }
 
-__global__ void scale_inv_real_kernel(double2* v, long n, const double* s, const int* skip) {
+__global__ void scale_inv_real_kernel(double2* v, long n, const double* s, const int* skip, float2* v32) {
     if (skip && *skip) return;
     const double d = *s;
     if (!(d != 0.0) || !isfinite(d)) return;
-    const double inv = 1.0 / d;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        double2 a = v[i];
-        v[i] = make_double2(a.x * inv, a.y * inv);
-    }
+    scale_rows(v, n, 1.0 / d, v32);
 }
 
 __global__ void sub_kernel(const double2* b, const double2* y, double2* r, long n) {
@@ -244,36 +329,9 @@ __global__ void sub_kernel(const double2* b, const double2* y, double2* r, long 
         r[i] = csub(b[i], y[i]);
 }
 
-template <bool ADD>
-__global__ void lincomb_kernel(const double2* __restrict__ V, long ldv, int k, const double2* __restrict__ c,
-                               double2* __restrict__ out, long n) {
-    __shared__ double2 cs[kMaxBasis];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = c[i];
-    __syncthreads();
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-        double2 s = ADD ? out[idx] : make_double2(0, 0);
-        for (int i = 0; i < k; i++) s = cadd(s, cmul(V[(long)i * ldv + idx], cs[i]));
-        out[idx] = s;
-    }
-}
-
-// z = x + V (M s); M: r x r column-major.  Each block forms c = M s redundantly.
-__global__ void defl_update_kernel(const double2* __restrict__ V, long ldv, int r, const double2* __restrict__ M,
-                                   const double2* __restrict__ s, const double2* x, double2* z, long n,
-                                   const int* skip) {
-    if (skip && *skip) return;
-    __shared__ double2 cs[kMaxBasis];
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-        double2 acc = make_double2(0, 0);
-        for (int q = 0; q < r; q++) acc = cadd(acc, cmul(M[(long)q * r + i], s[q]));
-        cs[i] = acc;
-    }
-    __syncthreads();
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-        double2 acc = x[idx];
-        for (int i = 0; i < r; i++) acc = cadd(acc, cmul(V[(long)i * ldv + idx], cs[i]));
-        z[idx] = acc;
-    }
+__global__ void to_c64_kernel(const double2* x, float2* y, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        y[i] = make_float2((float)x[i].x, (float)x[i].y);
 }
 
 __global__ void gmres_lsq_kernel(GmresDev S) {
@@ -285,7 +343,6 @@ __global__ void gmres_lsq_kernel(GmresDev S) {
         const double2 d = S.H[(long)i * ld + i];
         const double dd = d.x * d.x + d.y * d.y;
         if (dd == 0.0) { S.y[i] = make_double2(0, 0); *S.flags |= 4; continue; }
-        // acc / d
         S.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
     }
 }
@@ -306,41 +363,74 @@ static inline int grid_for(long n) {
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
-die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, double2* out, const RedScratch& rs,
-                  const int* skip, cudaStream_t st) {
-    if (nv > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS, st, dots_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, out, rs, skip));
+die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
+                  const RedScratch& rs, const int* skip, cudaStream_t st) {
+    if (nv + 1 > kMaxBasis || nv < 0) return DIE_EINVAL;
+    DIE_PROF(PK_DOTS, st, dots_kernel<double2><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, with_norm, out, rs, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_cgs_update_dots(const double2* V, long ldv, int nv, double2* w, long n, const double2* h, double2* out,
-                             const RedScratch& rs, const int* skip, cudaStream_t st) {
-    if (nv > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_UPDATE_DOTS, st, update_dots_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, h, out, rs, skip));
+die_status k_dots32(const float2* V, long ldv, int nv, const float2* w, long n, double2* out, const RedScratch& rs,
+                    const int* skip, cudaStream_t st) {
+    if (nv > kMaxBasis || nv < 0) return DIE_EINVAL;
+    DIE_PROF(PK_DOTS32, st, dots_kernel<float2><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, 0, out, rs, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_cgs_update_norm_givens(const double2* V, long ldv, int nv, double2* w, long n, GmresDev S, int j,
-                                    int step, const RedScratch& rs, cudaStream_t st) {
-    if (nv > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_UPDATE_NORM, st, update_norm_givens_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, S, j, step, rs));
+die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
+                        double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs, const int* skip,
+                        cudaStream_t st) {
+    if (k > kMaxBasis || k < 0) return DIE_EINVAL;
+    const Dgks d = dec ? *dec : Dgks{};
+    if (nrm2) {
+        DIE_PROF(PK_UPDATE_NORM, st, basis_axpy_kernel<double2, true><<<kRedBlocks, kRedThreads, 0, st>>>(
+                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nrm2, d, dec ? 1 : 0, rs, skip));
+    } else {
+        DIE_PROF(PK_LINCOMB, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
+                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nullptr, d, 0, rs, skip));
+    }
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_cgs_update_norm(const double2* V, long ldv, int nv, double2* w, long n, const double2* h, double2* out,
-                             const RedScratch& rs, const int* skip, cudaStream_t st) {
-    if (nv > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_UPDATE_NORM, st, update_norm_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, h, out, rs, skip));
+die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
+                         double2* z, long n, const int* skip, cudaStream_t st) {
+    if (r > kMaxBasis || r < 1) return DIE_EINVAL;
+    DIE_PROF(PK_DEFL_UPDATE, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
+                 V, ldv, r, nullptr, 1.0, M, s, x, z, n, nullptr, Dgks{}, 0, RedScratch{}, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st) {
-    DIE_PROF(PK_SCALE, st, scale_inv_sqrt_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, nrm2, skip));
+die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, const float2* x,
+                           float2* z, long n, const int* skip, cudaStream_t st) {
+    if (r > kMaxBasis || r < 1) return DIE_EINVAL;
+    DIE_PROF(PK_DEFL_UPDATE, st, defl_update32_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, M, s, x, z, n, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_scale_inv_real(double2* v, long n, const double* s, const int* skip, cudaStream_t st) {
-    DIE_PROF(PK_SCALE, st, scale_inv_real_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, s, skip));
+
+die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
+                    int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st) {
+    Dgks dec;
+    dec.before2 = h1 + nv;
+    dec.reorth = reorth;
+    dec.skip2 = skip2;
+    dec.done = done;
+    dec.always = eta2 >= 1.0 ? 1 : 0;
+    dec.eta2 = eta2;
+    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st));
+    DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st));
+    DIE_TRY(k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st));
+    DIE_TRY(k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, nullptr, rs, skip2, st));
+    return DIE_OK;
+}
+
+die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32) {
+    DIE_PROF(PK_SCALE, st, scale_inv_sqrt_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, nrm2, skip, v32));
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+die_status k_scale_inv_real(double2* v, long n, const double* s, const int* skip, cudaStream_t st, float2* v32) {
+    DIE_PROF(PK_SCALE, st, scale_inv_real_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, s, skip, v32));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -349,22 +439,13 @@ die_status k_sub(const double2* b, const double2* y, double2* r, long n, cudaStr
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_lincomb_add(const double2* V, long ldv, int k, const double2* c, double2* x, long n, cudaStream_t st) {
-    if (k > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_LINCOMB, st, lincomb_kernel<true><<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, k, c, x, n));
+die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st) {
+    DIE_PROF(PK_OTHER, st, to_c64_kernel<<<grid_for(n), kRedThreads, 0, st>>>(x, y, n));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_lincomb(const double2* V, long ldv, int k, const double2* c, double2* out, long n, cudaStream_t st) {
-    if (k > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_LINCOMB, st, lincomb_kernel<false><<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, k, c, out, n));
-    DIE_LAUNCH_CHECK();
-    return DIE_OK;
-}
-die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
-                         double2* z, long n, const int* skip, cudaStream_t st) {
-    if (r > kMaxBasis) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, defl_update_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, M, s, x, z, n, skip));
+die_status k_arnoldi_finish(GmresDev S, int j, int step, cudaStream_t st) {
+    DIE_PROF(PK_SMALL, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j, step));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -124,6 +124,7 @@ static void free_defl(defl_s* d) {
     if (!d) return;
     if (d->V) cudaFree(d->V);
     if (d->M) cudaFree(d->M);
+    if (d->V32) cudaFree(d->V32);
     if (d->s) cudaFree(d->s);
     free_red_scratch(&d->rs);
     delete d;
@@ -183,7 +184,7 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     // q_0: seeded random unit vector
     random_vector_kernel<<<1216, 256, 0, st>>>(w.Q, n, o->seed + 1);
     DIE_LAUNCH_CHECK();
-    DIE_TRY(k_dots(w.Q, 0, 1, w.Q, n, w.nrm, rs, nullptr, st));
+    DIE_TRY(k_dots(w.Q, 0, 0, w.Q, n, 1, w.nrm, rs, nullptr, st));
     DIE_TRY(k_scale_inv_sqrt(w.Q, n, w.nrm, nullptr, st));
 
     std::vector<double2> T(p * (size_t)p), bv(p);
@@ -194,12 +195,10 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
             double2* qj = w.Q + (long)j * n;
             double2* wv = w.Q + (long)(j + 1) * n;
             DIE_TRY(apply(qj, wv));
-            DIE_TRY(k_dots(w.Q, n, j + 1, wv, n, w.h1, rs, nullptr, st));
-            DIE_TRY(k_cgs_update_dots(w.Q, n, j + 1, wv, n, w.h1, w.h2, rs, nullptr, st));
-            DIE_TRY(k_cgs_update_norm(w.Q, n, j + 1, wv, n, w.h2, w.nrm, rs, nullptr, st));
-            ks_column_kernel<<<1, 128, 0, st>>>(w.B, p, j, w.h1, w.h2, w.nrm);
+            DIE_TRY(cgs_dgks(w.Q, n, j + 1, wv, n, w.h1, w.h2, w.nrm, w.ist + 1, w.ist + 2, nullptr, 1.0, rs, st));
+            ks_column_kernel<<<1, 128, 0, st>>>(w.B, p, j, w.h1, w.h2, w.nrm + 1);
             DIE_LAUNCH_CHECK();
-            DIE_TRY(k_scale_inv_sqrt(wv, n, w.nrm, nullptr, st));
+            DIE_TRY(k_scale_inv_sqrt(wv, n, w.nrm + 1, nullptr, st));
         }
         ks_small_kernel<<<1, 32, 0, st>>>(w.B, p, w.T, w.Z, w.bvec, w.work, w.ist);
         DIE_LAUNCH_CHECK();
@@ -267,21 +266,22 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     for (int j = 0; j < r; j++) {
         double2* vj = d->V + (long)j * n;
         if (j > 0) {
-            DIE_TRY(k_dots(d->V, n, j, vj, n, w.h1, rs, nullptr, st));
-            DIE_TRY(k_cgs_update_dots(d->V, n, j, vj, n, w.h1, w.h2, rs, nullptr, st));
-            DIE_TRY(k_cgs_update_norm(d->V, n, j, vj, n, w.h2, w.nrm, rs, nullptr, st));
+            DIE_TRY(cgs_dgks(d->V, n, j, vj, n, w.h1, w.h2, w.nrm, w.ist + 1, w.ist + 2, nullptr, 1.0, rs, st));
+            DIE_TRY(k_scale_inv_sqrt(vj, n, w.nrm + 1, nullptr, st));
         } else {
-            DIE_TRY(k_dots(vj, 0, 1, vj, n, w.nrm, rs, nullptr, st));
+            DIE_TRY(k_dots(vj, 0, 0, vj, n, 1, w.nrm, rs, nullptr, st));
+            DIE_TRY(k_scale_inv_sqrt(vj, n, w.nrm, nullptr, st));
         }
-        DIE_TRY(k_scale_inv_sqrt(vj, n, w.nrm, nullptr, st));
     }
     // T = V^* Atilde V in FP64 (Eq. (4.13)); column l: V^* (Atilde v_l)
     double2* AV = w.Q2;          // reuse: r vectors
     for (int l = 0; l < r; l++) {
         DIE_TRY(reg ? apply_reg<double, double2>(op, d->V + (long)l * n, AV, st)
                     : apply_op<double, double2>(op, Contrast::Chi, d->V + (long)l * n, AV, st));
-        DIE_TRY(k_dots(d->V, n, r, AV, n, d->M + (long)l * r, rs, nullptr, st));
+        DIE_TRY(k_dots(d->V, n, r, AV, n, 0, d->M + (long)l * r, rs, nullptr, st));
     }
+    DIE_TRY(dalloc((void**)&d->V32, (size_t)r * n * sizeof(float2)));
+    DIE_TRY(k_to_c64(d->V, d->V32, (long)r * n, st));
     inverse_minus_identity_kernel<<<1, 32, 0, st>>>(d->M, r, w.ist + 4, w.ist);
     DIE_LAUNCH_CHECK();
     int rc = 0;

@@ -113,6 +113,13 @@ __device__ __forceinline__ void dft(V* x) {
 }
 
 // ------------------------------------------------------------ stage primitives
+// Shared-memory arrays are padded by one slot per 16 elements: the stride-R stores of
+// the early stages (thread j writes j R + r) then fall in distinct banks.
+__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 4); }
+
+// j mod Ns (Ns is a power of two for 2^a transforms, possibly 3 * 2^b otherwise)
+__device__ __forceinline__ int mod_ns(int j, int Ns) { return (Ns & (Ns - 1)) == 0 ? (j & (Ns - 1)) : j % Ns; }
 // Thread t of a group of G threads handles butterflies j = t + b G, b < EPT/R.
 // Register x[b * R + r] holds input r of butterfly b.
 
@@ -124,7 +131,7 @@ __device__ __forceinline__ void stage_load(const V* __restrict__ buf, V (&x)[EPT
     for (int b = 0; b < B; b++) {
         const int j = t + b * G;
 #pragma unroll
-        for (int r = 0; r < R; r++) x[b * R + r] = buf[j + r * LR];
+        for (int r = 0; r < R; r++) x[b * R + r] = buf[pidx(j + r * LR)];
     }
 }
 
@@ -135,11 +142,12 @@ __device__ __forceinline__ void stage_compute(V (&x)[EPT], int L, int Ns, int t,
     for (int b = 0; b < B; b++) {
         const int j = t + b * G;
         if (Ns > 1) {
-            const int k = j % Ns;
-            const int step = (L / (Ns * R)) * k;
+            const int k = mod_ns(j, Ns);
+            const int LR = L / R;
+            const int step = ((Ns & (Ns - 1)) == 0 ? (LR >> (__ffs(Ns) - 1)) : LR / Ns) * k;
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                V w = tw[r * step];
+                V w = __ldg(&tw[r * step]);
                 if (INV) w.y = -w.y;
                 x[b * R + r] = cmul(x[b * R + r], w);
             }
@@ -154,10 +162,10 @@ __device__ __forceinline__ void stage_store(V* __restrict__ buf, const V (&x)[EP
 #pragma unroll
     for (int b = 0; b < B; b++) {
         const int j = t + b * G;
-        const int k = j % Ns;
+        const int k = mod_ns(j, Ns);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; r++) buf[base + r * Ns] = x[b * R + r];
+        for (int r = 0; r < R; r++) buf[pidx(base + r * Ns)] = x[b * R + r];
     }
 }
 
@@ -193,8 +201,28 @@ __device__ __forceinline__ void store_any(int R, V* buf, const V (&x)[EPT], int 
 // stage's input (first stage) or output (last stage, Ns = L/R), j = t + b G.
 template <int EPT>
 __device__ __forceinline__ int reg_index(int e, int R, int L, int t, int G) {
+    if ((R & (R - 1)) == 0) {
+        const int lg = __ffs(R) - 1;
+        return t + (e >> lg) * G + (e & (R - 1)) * (L >> lg);
+    }
     const int b = e / R, r = e - b * R;
     return t + b * G + r * (L / R);
+}
+
+// Plan of a power-of-two length known at compile time (the same radices as the host
+// planner): kernels instantiated for a fixed L use it so that every radix, stride and
+// index in the stage code is a constant.
+__host__ __device__ constexpr FftPlan pow2_plan(int L, bool reversed) {
+    FftPlan p{};
+    int a = 0;
+    while ((1 << a) < L) a++;
+    p.L = L;
+    p.ept = 16;
+    const int stages = (a + 3) / 4;
+    const int base = a / stages, extra = a % stages;
+    p.ns = stages;
+    for (int s = 0; s < stages; s++) p.radix[reversed ? stages - 1 - s : s] = 1 << (base + (s < extra ? 1 : 0));
+    return p;
 }
 
 // Run stages [s0, s1) of plan `pl` in place on `buf` (shared memory).  Every thread
@@ -204,6 +232,7 @@ template <typename V, int EPT, bool INV>
 __device__ __forceinline__ void run_stages(V* buf, const FftPlan& pl, int s0, int s1, int& Ns, const V* tw,
                                            int t, int G, bool active) {
     V x[EPT];
+#pragma unroll
     for (int s = s0; s < s1; s++) {
         const int R = pl.radix[s];
         if (active) load_any<V, EPT>(R, buf, x, pl.L, t, G);

@@ -1,14 +1,21 @@
 // Restarted GMRES(m) (Saad & Schultz) on Atilde = A or A_R A (Section 5), with the
 // deflating right preconditioner of Eq. (4.12): Atilde P^-1 v = btilde, x = P^-1 v.
 //
-// One cycle runs entirely on the device without host round trips: the Arnoldi
-// vectors are orthogonalised by CGS2 (three fused sweeps: projections;
-// update + re-projection; update + norm), the new column of the Hessenberg matrix
-// is rotated by Givens rotations on the device, and when the residual estimate
-// reaches tol a device flag makes the remaining kernels of the cycle return at
-// once.  The host reads one flag set per cycle.  Between cycles the residual
-// btilde - Atilde x is recomputed in FP64 (in the FP32-inner form this is the
-// iterative-refinement step).
+// One cycle runs entirely on the device without host round trips: each Arnoldi
+// vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion (a
+// second pass only when the first one cancelled more than half of ||w||^2; the
+// device decides, and the second-pass kernels return at once when it is not
+// needed), the new Hessenberg column is rotated by Givens rotations on the device,
+// and when the residual estimate reaches tol a device flag makes the remaining
+// kernels of the cycle return at once.  The host reads one flag set per cycle.
+// Between cycles the residual btilde - Atilde x is recomputed in FP64 (in the
+// FP32-inner form this is the iterative-refinement step).
+//
+// FP32-inner form: the products with Atilde inside a cycle run in complex64 and the
+// deflation P^-1 uses a complex64 copy of V with FP32 sums (P^-1 is one fixed
+// preconditioner for the whole solve, so its rounding only changes the
+// preconditioner, and the FP64 restart residual corrects the iterate).  Arnoldi,
+// least squares and the restart residual are FP64 in both forms.
 #include <math.h>
 #include <string.h>
 
@@ -43,7 +50,7 @@ SolverCache* solver_cache(dieop_s* op) { return reinterpret_cast<SolverCache*>(o
 void free_solver_cache(dieop_s* op) {
     SolverCache* c = solver_cache(op);
     if (!c) return;
-    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->small, c->hist, c->ints, c->wnorm, c->one};
+    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->wnorm, c->one};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_red_scratch(&c->rs);
@@ -53,7 +60,7 @@ void free_solver_cache(dieop_s* op) {
     op->solver = nullptr;
 }
 
-static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 4 * (m + 2) + 8; }
+static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 4 * (m + 3) + 16; }
 
 die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     SolverCache* c = solver_cache(op);
@@ -72,8 +79,9 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     auto al = [](void** p, size_t b) { return cudaMalloc(p, b) == cudaSuccess; };
     bool ok = al((void**)&c->V, (size_t)(m + 1) * n * sizeof(double2)) && al((void**)&c->btil, n * sizeof(double2)) &&
               al((void**)&c->tmp, n * sizeof(double2)) && al((void**)&c->z, n * sizeof(double2)) &&
+              al((void**)&c->v32, n * sizeof(float2)) && al((void**)&c->z32, n * sizeof(float2)) &&
               al((void**)&c->small, small_count(m) * sizeof(double2)) &&
-              al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) && al((void**)&c->ints, 8 * sizeof(int)) &&
+              al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) && al((void**)&c->ints, 16 * sizeof(int)) &&
               al((void**)&c->wnorm, 8 * sizeof(double)) && al((void**)&c->one, sizeof(double2));
     if (!ok) {
         cudaGetLastError();
@@ -94,8 +102,14 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
 }
 
 die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st) {
-    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, d->s, d->rs, skip, st));
+    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, 0, d->s, d->rs, skip, st));
     DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
+    return DIE_OK;
+}
+
+die_status defl_apply32(defl_s* d, const float2* x, float2* z, const int* skip, cudaStream_t st) {
+    DIE_TRY(k_dots32(d->V32, d->n, d->r, x, d->n, d->s, d->rs, skip, st));
+    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
@@ -116,7 +130,7 @@ static die_status apply_inner(dieop_s* op, bool reg, bool mixed, const double2* 
 // ||v||^2 read back to the host (synchronises the stream).
 static die_status norm2_host(SolverCache* c, const double2* v, long n, double2* dev_out, double* host_out,
                              cudaStream_t st) {
-    DIE_TRY(k_dots(v, 0, 1, v, n, dev_out, c->rs, nullptr, st));
+    DIE_TRY(k_dots(v, 0, 0, v, n, 1, dev_out, c->rs, nullptr, st));
     DIE_CUDA_TRY(cudaMemcpyAsync(c->host, dev_out, sizeof(double2), cudaMemcpyDeviceToHost, st));
     DIE_CUDA_TRY(cudaStreamSynchronize(st));
     *host_out = c->host[0];
@@ -140,6 +154,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
+    const double eta = o->reorth_eta > 0 ? o->reorth_eta : 0.01;
+    const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
     const int m = o->restart;
     const long n = 2L * op->N;
     const int hist_cap = o->max_iters < (1 << 22) ? (o->max_iters > 0 ? o->max_iters : 1) : (1 << 22);
@@ -154,20 +170,25 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     S.H = sm; sm += (size_t)(m + 1) * m;
     S.cs = sm; sm += m;
     S.sn = sm; sm += m;
-    S.g = sm; sm += m + 2;
-    S.h1 = sm; sm += m + 2;
-    S.h2 = sm; sm += m + 2;
-    S.y = sm; sm += m + 2;
+    S.g = sm; sm += m + 3;
+    S.h1 = sm; sm += m + 3;
+    S.h2 = sm; sm += m + 3;
+    S.y = sm; sm += m + 3;
+    S.nrm = sm; sm += 4;
     double2* scal = sm;            // scalars: [0] residual norm^2
     S.hist = c->hist;
     S.done = c->ints;
     S.k = c->ints + 1;
     S.flags = c->ints + 2;
+    S.reorth = c->ints + 3;
+    S.skip2 = c->ints + 4;
+    S.nreorth = c->ints + 5;
     S.wnorm = c->wnorm;
     S.m = m;
+    S.jmax = m;
     S.hist_cap = c->hist_cap;
     S.tol = o->tol;
-    DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, 8 * sizeof(int), st));
+    DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, 16 * sizeof(int), st));
 
     // right-hand side of the solved system
     const double2* bt = b;
@@ -189,6 +210,10 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     double rel = 0, t_mv = 0, t_orth = 0, t_defl = 0;
     const long ldv = n;
     double2* V = c->V;
+    // FP32-inner with deflation: P^-1 v_j and the product input stay complex64; the
+    // normalising kernel keeps a complex64 copy of the current Arnoldi vector.
+    const bool defl32 = defl && mixed;
+    float2* v32 = defl32 ? c->v32 : nullptr;
     if (bnorm == 0.0) {
         DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
         status = DIE_OK;
@@ -208,7 +233,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (!isfinite(rel)) { status = DIE_ENAN; break; }
         if (rel <= o->tol) { status = DIE_OK; break; }
         if (iters >= o->max_iters) break;
-        DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st));
+        DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32));
         DIE_TRY(k_gmres_init(S, scal, st));
         const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
         S.jmax = jmax;
@@ -216,22 +241,28 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
             const double2* vj = V + (long)j * ldv;
             double2* w = V + (long)(j + 1) * ldv;
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j], st));
-            const double2* src = vj;
-            if (defl) {
-                DIE_TRY(defl_apply(defl, vj, c->z, S.done, st));
-                src = c->z;
+            if (defl32) {
+                DIE_TRY(defl_apply32(defl, c->v32, c->z32, S.done, st));
+                if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
+                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
+                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
+            } else {
+                const double2* src = vj;
+                if (defl) {
+                    DIE_TRY(defl_apply(defl, vj, c->z, S.done, st));
+                    src = c->z;
+                }
+                if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
+                DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st));
             }
-            if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
-            DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
-            DIE_TRY(k_dots(V, ldv, j + 2, w, n, S.h1, c->rs, S.done, st));
-            DIE_TRY(k_cgs_update_dots(V, ldv, j + 1, w, n, S.h1, S.h2, c->rs, S.done, st));
-            DIE_TRY(k_cgs_update_norm_givens(V, ldv, j + 1, w, n, S, j, iters + j, c->rs, st));
-            DIE_TRY(k_scale_inv_real(w, n, S.wnorm, S.done, st));
+            DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1, S.h2, S.nrm, S.reorth, S.skip2, S.done, eta2, c->rs, st));
+            DIE_TRY(k_arnoldi_finish(S, j, iters + j, st));
+            DIE_TRY(k_scale_inv_real(w, n, S.wnorm, S.done, st, v32));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
         }
-        int hk[4];
-        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        int hk[8];
+        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(hk, c->host, sizeof hk);
         const int k = hk[1], flags = hk[2];
@@ -252,14 +283,14 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (k == 0) { status = DIE_EBREAKDOWN; break; }
         DIE_TRY(k_gmres_lsq(S, st));
         if (defl) {
-            DIE_TRY(k_lincomb(V, ldv, k, S.y, c->tmp, n, st));
+            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, nullptr, c->tmp, n, nullptr, nullptr, c->rs, nullptr, st));
             DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st));
-            DIE_TRY(k_lincomb_add(c->tmp, ldv, 1, c->one, x, n, st));
+            DIE_TRY(k_basis_axpy(c->tmp, ldv, 1, c->one, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
         } else {
-            DIE_TRY(k_lincomb_add(V, ldv, k, S.y, x, n, st));
+            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
         }
         // a singular triangular factor (breakdown with no exact solution) shows up after the LSQ
-        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(hk, c->host, sizeof hk);
         if (hk[2] & 4) { status = DIE_EBREAKDOWN; break; }
@@ -274,7 +305,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         DIE_TRY(norm2_host(c, b, n, scal, &b2, st));
         rel_orig = b2 > 0 ? sqrt(r2 / b2) : 0.0;
     }
-    DIE_CUDA_TRY(cudaStreamSynchronize(st));
+    int nre = 0;
+    DIE_CUDA_TRY(cudaMemcpy(&nre, S.nreorth, sizeof(int), cudaMemcpyDeviceToHost));
     if (rep) {
         rep->cycles = cycles;
         rep->iters = iters;
@@ -286,6 +318,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         rep->t_defl = t_defl;
         rep->t_total = seconds_since(t0);
         rep->history_len = 0;
+        rep->n_reorth = nre;
         if (rep->history && rep->history_cap > 0 && hist_len > 0) {
             const int cnt = hist_len < rep->history_cap ? hist_len : rep->history_cap;
             DIE_CUDA_TRY(cudaMemcpy(rep->history, c->hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));

@@ -72,11 +72,11 @@ __global__ void fft_lines_kernel(double2* data, long elem_stride, long line_stri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);
     double2* line = data + blockIdx.x * line_stride;
-    for (int e = threadIdx.x; e < pl.L; e += blockDim.x) buf[e] = line[e * elem_stride];
+    for (int e = threadIdx.x; e < pl.L; e += blockDim.x) buf[pidx(e)] = line[e * elem_stride];
     __syncthreads();
     int Ns = 1;
     run_stages<double2, EPT, false>(buf, pl, 0, pl.ns, Ns, tw, threadIdx.x, blockDim.x, true);
-    for (int e = threadIdx.x; e < pl.L; e += blockDim.x) line[e * elem_stride] = buf[e];
+    for (int e = threadIdx.x; e < pl.L; e += blockDim.x) line[e * elem_stride] = buf[pidx(e)];
 }
 
 // gq[plane][k1q][k2q] = spectrum[plane][k2q][k1q] / (M1 M2), k1q <= M1/2, k2q <= M2/2.
@@ -97,7 +97,7 @@ __global__ void quarter_kernel(const double2* __restrict__ spec, int M1, int M2,
 static die_status fft_lines(double2* data, long elem_stride, long line_stride, int nlines, const FftPlan& pl,
                             const double2* tw, cudaStream_t st) {
     const int G = pl.L / pl.ept;
-    const size_t smem = (size_t)pl.L * sizeof(double2);
+    const size_t smem = (size_t)padded_len(pl.L) * sizeof(double2);
     if (pl.ept == 16) {
         DIE_CUDA_TRY(cudaFuncSetAttribute(fft_lines_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         fft_lines_kernel<16><<<nlines, G, smem, st>>>(data, elem_stride, line_stride, pl, tw);

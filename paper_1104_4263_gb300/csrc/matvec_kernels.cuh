@@ -1,0 +1,477 @@
+// FFT-speed products with the discretised TE operator A = I - G X (Eqs. (4.3)-(4.5)):
+// kernels and launchers, included by the instantiation units matvec.cu (FP64) and
+// matvec_f32.cu (complex64 arithmetic).
+//
+// G is block-Toeplitz (its entries depend on x_n - x_m only), so G w is a 2-D
+// linear convolution of the 2 x 2 Green's tensor table with the contrast current
+// w = chi u; it is computed with zero padding to M1 x M2 >= (2 n1) x (2 n2):
+//
+//   K1  per grid row i2 and component: w = chi * u, zero-pad to M1, FFT along x1,
+//       written transposed: W[c][k1][i2]                    (rows i2 < n2 only)
+//   K2  per column k1: FFT along x2 (inputs i2 >= n2 are zero), multiply by the
+//       Green spectra  z1 = G11 w1 + G12 w2, z2 = G12 w1 + G22 w2, inverse FFT,
+//       keep i2 < n2, written back in place
+//   K3  per grid row: inverse FFT along x1, keep i1 < n1, y = u - z
+//   K3K1 (regularised product A(chi') A(chi), Section 5) finishes row i2 of the
+//       first product (v = u - z, kept in a buffer for the final subtraction) and
+//       immediately starts the second product on the same row: chi' * v, FFT.
+//
+// The spectra are stored for k1 <= M1/2, k2 <= M2/2 only: G11, G22 are even and
+// G12 is odd in each offset coordinate (a symmetry of Eqs. (4.3)-(4.5)), so the
+// other quadrants follow by sign.  They carry the 1/(M1 M2) of the inverse FFTs.
+//
+// Every kernel takes a compile-time transform length LS: LS = 0 reads the plan from
+// the operator at run time (any 2^a or 3 * 2^a length); LS = 2^a fixes the plan at
+// compile time so that radices, strides and indices are constants.
+#pragma once
+
+#include "op.cuh"
+#include "prof.cuh"
+
+namespace die {
+
+// Rows per block of the row passes: enough for 32-byte segments in the transposed
+// accesses (4 complex64 / 2 complex128), at most 512 threads per block.
+template <typename C> constexpr int tile_rows() { return sizeof(C) == 8 ? 4 : 2; }
+constexpr int kRowsMaxThreads = 512;
+constexpr size_t kStageGreenMaxSmem = 200 * 1024;
+
+template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+
+// Row stride of the row-pass tiles: the padded length plus two slots, so that the TR
+// rows (whose lengths are multiples of 128 bytes) start in different banks.
+__host__ __device__ __forceinline__ int tile_stride(int L) { return padded_len(L) + 2; }
+
+// ------------------------------------------------------------------------- K1
+template <typename T, typename IO, int EPT, int LS>
+__global__ void __launch_bounds__(512) k1_rows_fwd(OpDev<T> op, const IO* __restrict__ u,
+                                                   const C_t<T>* __restrict__ chi, C_t<T>* __restrict__ W,
+                                                   const int* __restrict__ skip) {
+    using C = C_t<T>;
+    if (skip && *skip) return;
+    constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false);
+    const FftPlan pl = LS ? kf : op.f1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int L = LS ? LS : op.M1, G = L / EPT, TR = blockDim.x / G;
+    const int rs = threadIdx.x / G, t = threadIdx.x - rs * G;
+    const int c = blockIdx.y;
+    const int i2_0 = blockIdx.x * TR;
+    const int i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    const long N = (long)op.n1 * op.n2;
+    const int Lp = tile_stride(L);
+    C* buf = tile + rs * Lp;
+    int Ns = 1;
+    {
+        const int R = pl.radix[0];
+        C x[EPT];
+        if (active) {
+            const IO* urow = u + c * N + (long)i2 * op.n1;
+            const C* crow = chi + (long)i2 * op.n1;
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                x[e] = idx < op.n1 ? cmul(cvt<C>(urow[idx]), crow[idx]) : czero<C>();
+            }
+            compute_any<C, EPT, false>(R, x, L, 1, t, G, op.tw1);
+            store_any<C, EPT>(R, buf, x, L, 1, t, G);
+        }
+        __syncthreads();
+        Ns = R;
+    }
+    run_stages<C, EPT, false>(buf, pl, 1, pl.ns, Ns, op.tw1, t, G, active);
+    for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
+        const int k1 = e / TR, r = e - k1 * TR;
+        const int row = i2_0 + r;
+        if (row < op.n2) W[((long)c * L + k1) * op.n2 + row] = tile[r * Lp + pidx(k1)];
+    }
+}
+
+// ------------------------------------------------------------------------- K2
+// One block per column k1: threads [0, G) transform component 0 and [G, 2G)
+// component 1, each holding EPT values.  The forward transforms end in shared memory
+// in natural order; at the Green multiply every thread reads both components at the
+// indices of its first inverse stage.  The column's quarter spectra are staged into
+// shared memory at the start (when they fit), so their latency overlaps the FFT.
+template <typename T, int EPT, int LS>
+__global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__ W, int stage_g,
+                                               const int* __restrict__ skip) {
+    using C = C_t<T>;
+    if (skip && *skip) return;
+    constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
+    const int nsf = LS ? kf.ns : op.f2.ns, nsi = LS ? ki.ns : op.i2.ns;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = LS ? LS : op.M2, G = L / EPT, Lp = padded_len(L);
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + Lp;
+    C* gs = buf1 + Lp;                          // 3 x Q2 spectra of this column (if staged)
+    const int comp = threadIdx.x >= G ? 1 : 0;
+    const int t = threadIdx.x - comp * G;
+    C* buf = comp ? buf1 : buf0;
+    const int k1 = blockIdx.x;
+    C* col = W + ((long)comp * op.M1 + k1) * op.n2;
+    const int h1 = op.M1 >> 1, h2 = L >> 1;
+    const int Q2 = h2 + 1;
+    const int k1q = k1 <= h1 ? k1 : op.M1 - k1;
+    const bool neg1 = k1 > h1;
+    const long plane = (long)op.Q1 * Q2;
+    const C* g = op.gq + (long)k1q * Q2;
+    if (stage_g) {
+        for (int e = threadIdx.x; e < 3 * Q2; e += blockDim.x) {
+            const int pl = e / Q2, q = e - pl * Q2;
+            gs[e] = g[pl * plane + q];
+        }
+    }
+    C x[EPT];
+    int Ns = 1;
+#pragma unroll
+    for (int s = 0; s < nsf; s++) {
+        const int R = LS ? kf.radix[s] : op.f2.radix[s];
+        if (s == 0) {
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                x[e] = idx < op.n2 ? col[idx] : czero<C>();
+            }
+        } else {
+            load_any<C, EPT>(R, buf, x, L, t, G);
+            __syncthreads();
+        }
+        compute_any<C, EPT, false>(R, x, L, Ns, t, G, op.tw2);
+        store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+        __syncthreads();
+        Ns *= R;
+    }
+    {   // 2 x 2 Green-spectrum multiply at frequencies (k1, k2)
+        const int R = LS ? ki.radix[0] : op.i2.radix[0];
+#pragma unroll
+        for (int e = 0; e < EPT; e++) {
+            const int k2 = reg_index<EPT>(e, R, L, t, G);
+            const int k2q = k2 <= h2 ? k2 : L - k2;
+            const bool neg = neg1 != (k2 > h2);
+            const C a = buf0[pidx(k2)], b = buf1[pidx(k2)];
+            C gd, go;                           // diagonal (G11 or G22) and off-diagonal G12
+            if (stage_g) { gd = gs[comp * Q2 + k2q]; go = gs[2 * Q2 + k2q]; }
+            else { gd = g[comp * plane + k2q]; go = g[2 * plane + k2q]; }
+            if (neg) { go.x = -go.x; go.y = -go.y; }
+            x[e] = comp == 0 ? cadd(cmul(gd, a), cmul(go, b)) : cadd(cmul(go, a), cmul(gd, b));
+        }
+    }
+    __syncthreads();
+    Ns = 1;
+#pragma unroll
+    for (int s = 0; s < nsi; s++) {
+        const int R = LS ? ki.radix[s] : op.i2.radix[s];
+        if (s > 0) {
+            load_any<C, EPT>(R, buf, x, L, t, G);
+            __syncthreads();
+        }
+        compute_any<C, EPT, true>(R, x, L, Ns, t, G, op.tw2);
+        if (s < nsi - 1) {
+            store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                if (idx < op.n2) col[idx] = x[e];
+            }
+        }
+        Ns *= R;
+    }
+}
+
+// Load the transposed tile W[c][0..M1)[i2_0 .. i2_0+TR) into shared memory rows.
+template <typename C>
+__device__ __forceinline__ void load_tile(C* tile, const C* __restrict__ W, int c, int i2_0, int M1, int n2, int TR) {
+    const int Lp = tile_stride(M1);
+    for (int e = threadIdx.x; e < M1 * TR; e += blockDim.x) {
+        const int k1 = e / TR, r = e - k1 * TR;
+        const int row = i2_0 + r;
+        tile[r * Lp + pidx(k1)] = row < n2 ? W[((long)c * M1 + k1) * n2 + row] : czero<C>();
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------- K3
+// y = u - z for one tile of rows; u of element type U, y of IO.
+template <typename T, typename U, typename IO, int EPT, int LS>
+__global__ void __launch_bounds__(512) k3_rows_inv(OpDev<T> op, const C_t<T>* __restrict__ W,
+                                                   const U* __restrict__ u, IO* __restrict__ y,
+                                                   const int* __restrict__ skip) {
+    using C = C_t<T>;
+    if (skip && *skip) return;
+    constexpr FftPlan ki = pow2_plan(LS ? LS : 16, true);
+    const FftPlan iv = LS ? ki : op.i1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int L = LS ? LS : op.M1, G = L / EPT, TR = blockDim.x / G;
+    const int rs = threadIdx.x / G, t = threadIdx.x - rs * G;
+    const int c = blockIdx.y;
+    const int i2_0 = blockIdx.x * TR;
+    const int i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    const long N = (long)op.n1 * op.n2;
+    C* buf = tile + rs * tile_stride(L);
+    load_tile<C>(tile, W, c, i2_0, L, op.n2, TR);
+    int Ns = 1;
+    C x[EPT];
+#pragma unroll
+    for (int s = 0; s < iv.ns; s++) {
+        const int R = iv.radix[s];
+        if (active) load_any<C, EPT>(R, buf, x, L, t, G);
+        __syncthreads();
+        if (active) compute_any<C, EPT, true>(R, x, L, Ns, t, G, op.tw1);
+        if (s < iv.ns - 1) {
+            if (active) store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+            __syncthreads();
+        } else if (active) {
+            const long off = c * N + (long)i2 * op.n1;
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                if (idx < op.n1) y[off + idx] = csub(cvt<IO>(u[off + idx]), cvt<IO>(x[e]));
+            }
+        }
+        Ns *= R;
+    }
+}
+
+// ----------------------------------------------------------------------- K3K1
+template <typename T, typename IO, int EPT, int LS>
+__global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict__ W, const IO* __restrict__ u,
+                                                 const C_t<T>* __restrict__ chir, C_t<T>* __restrict__ vbuf,
+                                                 const int* __restrict__ skip) {
+    using C = C_t<T>;
+    if (skip && *skip) return;
+    constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
+    const FftPlan f = LS ? kf : op.f1;
+    const FftPlan iv = LS ? ki : op.i1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int L = LS ? LS : op.M1, G = L / EPT, TR = blockDim.x / G;
+    const int rs = threadIdx.x / G, t = threadIdx.x - rs * G;
+    const int c = blockIdx.y;
+    const int i2_0 = blockIdx.x * TR;
+    const int i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    const long N = (long)op.n1 * op.n2;
+    C* buf = tile + rs * tile_stride(L);
+    load_tile<C>(tile, W, c, i2_0, L, op.n2, TR);
+    int Ns = 1;
+    C x[EPT];
+#pragma unroll
+    for (int s = 0; s < iv.ns; s++) {
+        const int R = iv.radix[s];
+        if (active) load_any<C, EPT>(R, buf, x, L, t, G);
+        __syncthreads();
+        if (active) compute_any<C, EPT, true>(R, x, L, Ns, t, G, op.tw1);
+        if (s < iv.ns - 1) {
+            if (active) store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+            __syncthreads();
+        }
+        Ns *= R;
+    }
+    // v = u - z (first product), kept for the final subtraction; then chi' v -> FFT.
+    {
+        const int R = iv.radix[iv.ns - 1];      // == f.radix[0]: inverse plan is the reversed forward plan
+        if (active) {
+            const long off = c * N + (long)i2 * op.n1;
+            const C* crow = chir + (long)i2 * op.n1;
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                if (idx < op.n1) {
+                    const C v = csub(cvt<C>(u[off + idx]), x[e]);
+                    vbuf[off + idx] = v;
+                    x[e] = cmul(v, crow[idx]);
+                } else {
+                    x[e] = czero<C>();
+                }
+            }
+            compute_any<C, EPT, false>(R, x, L, 1, t, G, op.tw1);
+            store_any<C, EPT>(R, buf, x, L, 1, t, G);
+        }
+        __syncthreads();
+        Ns = R;
+    }
+    run_stages<C, EPT, false>(buf, f, 1, f.ns, Ns, op.tw1, t, G, active);
+    const int Lp = tile_stride(L);
+    for (int e = threadIdx.x; e < L * TR; e += blockDim.x) {
+        const int k1 = e / TR, r = e - k1 * TR;
+        const int row = i2_0 + r;
+        if (row < op.n2) W[((long)c * L + k1) * op.n2 + row] = tile[r * Lp + pidx(k1)];
+    }
+}
+
+// --------------------------------------------------------------------- launch
+struct Launch { dim3 grid, block; size_t smem; };
+
+template <typename T>
+inline Launch rows_launch(const OpDev<T>& v) {
+    using C = C_t<T>;
+    const int G = v.M1 / v.f1.ept;
+    int TR = tile_rows<C>();
+    while (TR > 1 && TR * G > kRowsMaxThreads) TR /= 2;
+    return Launch{dim3((v.n2 + TR - 1) / TR, 2), dim3(TR * G), (size_t)TR * tile_stride(v.M1) * sizeof(C)};
+}
+
+template <typename T>
+inline Launch cols_launch(const OpDev<T>& v, int* stage_g) {
+    using C = C_t<T>;
+    const size_t base = (size_t)2 * padded_len(v.M2) * sizeof(C);
+    const size_t staged = base + (size_t)3 * v.Q2 * sizeof(C);
+    *stage_g = staged <= kStageGreenMaxSmem ? 1 : 0;
+    return Launch{dim3(v.M1), dim3(2 * (v.M2 / v.f2.ept)), *stage_g ? staged : base};
+}
+
+// Launch a kernel instantiation, raising its dynamic shared-memory limit on first use.
+template <typename K, typename... Args>
+inline void launch_kernel(K kernel, bool& attr_set, const Launch& l, cudaStream_t st, Args... args) {
+    if (!attr_set) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set = true;
+    }
+    kernel<<<l.grid, l.block, l.smem, st>>>(args...);
+}
+
+// Compile-time lengths with a dedicated instantiation; anything else takes the runtime plan.
+#define DIE_POW2_SWITCH(M, CASE, DEFAULT) \
+    switch (M) {                          \
+        case 64: CASE(64); break;         \
+        case 128: CASE(128); break;       \
+        case 256: CASE(256); break;       \
+        case 512: CASE(512); break;       \
+        case 1024: CASE(1024); break;     \
+        case 2048: CASE(2048); break;     \
+        case 4096: CASE(4096); break;     \
+        default: DEFAULT; break;          \
+    }
+
+template <typename T, typename IO>
+inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st) {
+    const Launch l = rows_launch(v);
+#define K1_CASE(LSV) { static bool a_ = false; launch_kernel(k1_rows_fwd<T, IO, 16, LSV>, a_, l, st, v, u, chi, W, skip); }
+#define K1_DEF { static bool a16 = false, a12 = false;                                                     \
+                 if (v.f1.ept == 16) launch_kernel(k1_rows_fwd<T, IO, 16, 0>, a16, l, st, v, u, chi, W, skip); \
+                 else launch_kernel(k1_rows_fwd<T, IO, 12, 0>, a12, l, st, v, u, chi, W, skip); }
+    DIE_PROF(PK_ROWS_FWD, st, DIE_POW2_SWITCH(v.M1, K1_CASE, K1_DEF));
+#undef K1_CASE
+#undef K1_DEF
+}
+
+template <typename T>
+inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_t st) {
+    int sg = 0;
+    const Launch l = cols_launch(v, &sg);
+#define K2_CASE(LSV) { static bool a_ = false; launch_kernel(k2_cols<T, 16, LSV>, a_, l, st, v, W, sg, skip); }
+#define K2_DEF { static bool a16 = false, a12 = false;                                            \
+                 if (v.f2.ept == 16) launch_kernel(k2_cols<T, 16, 0>, a16, l, st, v, W, sg, skip); \
+                 else launch_kernel(k2_cols<T, 12, 0>, a12, l, st, v, W, sg, skip); }
+    DIE_PROF(PK_COLS, st, DIE_POW2_SWITCH(v.M2, K2_CASE, K2_DEF));
+#undef K2_CASE
+#undef K2_DEF
+}
+
+template <typename T, typename U, typename IO>
+inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st) {
+    const Launch l = rows_launch(v);
+#define K3_CASE(LSV) { static bool a_ = false; launch_kernel(k3_rows_inv<T, U, IO, 16, LSV>, a_, l, st, v, W, u, y, skip); }
+#define K3_DEF { static bool a16 = false, a12 = false;                                                    \
+                 if (v.f1.ept == 16) launch_kernel(k3_rows_inv<T, U, IO, 16, 0>, a16, l, st, v, W, u, y, skip); \
+                 else launch_kernel(k3_rows_inv<T, U, IO, 12, 0>, a12, l, st, v, W, u, y, skip); }
+    DIE_PROF(PK_ROWS_INV, st, DIE_POW2_SWITCH(v.M1, K3_CASE, K3_DEF));
+#undef K3_CASE
+#undef K3_DEF
+}
+
+template <typename T, typename IO>
+inline void launch_k3k1(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
+                        cudaStream_t st) {
+    const Launch l = rows_launch(v);
+#define KK_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_rows<T, IO, 16, LSV>, a_, l, st, v, W, u, chir, vb, skip); }
+#define KK_DEF { static bool a16 = false, a12 = false;                                                        \
+                 if (v.f1.ept == 16) launch_kernel(k3k1_rows<T, IO, 16, 0>, a16, l, st, v, W, u, chir, vb, skip); \
+                 else launch_kernel(k3k1_rows<T, IO, 12, 0>, a12, l, st, v, W, u, chir, vb, skip); }
+    DIE_PROF(PK_ROWS_INV_FWD, st, DIE_POW2_SWITCH(v.M1, KK_CASE, KK_DEF));
+#undef KK_CASE
+#undef KK_DEF
+}
+
+template <typename T> struct Sel;
+template <> struct Sel<double> {
+    static const double2* chi(const dieop_s* o, Contrast c) { return c == Contrast::Chi ? o->chi_d : o->chir_d; }
+    static OpDev<double> view(const dieop_s* o) { return view_d(o); }
+};
+template <> struct Sel<float> {
+    static const float2* chi(const dieop_s* o, Contrast c) { return c == Contrast::Chi ? o->chi_f : o->chir_f; }
+    static OpDev<float> view(const dieop_s* o) { return view_f(o); }
+};
+
+template <typename T, typename IO>
+die_status apply_op_skip(dieop_s* op, Contrast which, const IO* x, IO* y, const int* skip, cudaStream_t st) {
+    using C = C_t<T>;
+    const OpDev<T> v = Sel<T>::view(op);
+    C* W = reinterpret_cast<C*>(op->ws.W);
+    launch_k1<T, IO>(v, x, Sel<T>::chi(op, which), W, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3<T, IO, IO>(v, W, x, y, skip, st);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+template <typename T, typename IO>
+die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st) {
+    using C = C_t<T>;
+    const OpDev<T> v = Sel<T>::view(op);
+    C* W = reinterpret_cast<C*>(op->ws.W);
+    C* vb = reinterpret_cast<C*>(op->ws.v);
+    launch_k1<T, IO>(v, x, Sel<T>::chi(op, Contrast::Chi), W, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3k1<T, IO>(v, W, x, Sel<T>::chi(op, Contrast::ChiReg), vb, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3<T, C, IO>(v, W, vb, y, skip, st);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+// Input and output of different element types (complex64 in, complex128 out: the
+// products of the FP32-inner solves whose right preconditioner runs in complex64).
+template <typename T, typename IX, typename IY>
+die_status apply_op_skip_xy(dieop_s* op, Contrast which, const IX* x, IY* y, const int* skip, cudaStream_t st) {
+    using C = C_t<T>;
+    const OpDev<T> v = Sel<T>::view(op);
+    C* W = reinterpret_cast<C*>(op->ws.W);
+    launch_k1<T, IX>(v, x, Sel<T>::chi(op, which), W, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3<T, IX, IY>(v, W, x, y, skip, st);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+template <typename T, typename IX, typename IY>
+die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st) {
+    using C = C_t<T>;
+    const OpDev<T> v = Sel<T>::view(op);
+    C* W = reinterpret_cast<C*>(op->ws.W);
+    C* vb = reinterpret_cast<C*>(op->ws.v);
+    launch_k1<T, IX>(v, x, Sel<T>::chi(op, Contrast::Chi), W, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3k1<T, IX>(v, W, x, Sel<T>::chi(op, Contrast::ChiReg), vb, skip, st);
+    launch_k2<T>(v, W, skip, st);
+    launch_k3<T, C, IY>(v, W, vb, y, skip, st);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+template <typename T, typename IO>
+die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st) {
+    return apply_op_skip<T, IO>(op, c, x, y, nullptr, st);
+}
+template <typename T, typename IO>
+die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st) {
+    return apply_reg_skip<T, IO>(op, x, y, nullptr, st);
+}
+
+}  // namespace die

@@ -58,7 +58,7 @@ extern "C" die_status deflation_apply_noalloc(defl_t d, const void* x, void* z, 
     double2* s = base + kNoAllocPartials;
     // the reduction's arrival counter must start at zero
     DIE_CUDA_TRY(cudaMemsetAsync(rs.counter, 0, sizeof(unsigned), st));
-    DIE_TRY(k_dots(d->V, d->n, d->r, (const double2*)x, d->n, s, rs, nullptr, st));
+    DIE_TRY(k_dots(d->V, d->n, d->r, (const double2*)x, d->n, 0, s, rs, nullptr, st));
     DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, s, (const double2*)x, (double2*)z, d->n, nullptr, st));
     return DIE_OK;
 }

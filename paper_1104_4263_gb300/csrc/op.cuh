@@ -64,6 +64,12 @@ die_status apply_op_skip(dieop_s* op, Contrast c, const IO* x, IO* y, const int*
 template <typename T, typename IO>
 die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st);
 
+// Input and output of different element types (complex64 in, complex128 out).
+template <typename T, typename IX, typename IY>
+die_status apply_op_skip_xy(dieop_s* op, Contrast c, const IX* x, IY* y, const int* skip, cudaStream_t st);
+template <typename T, typename IX, typename IY>
+die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st);
+
 die_status set_kernel_attributes(const dieop_s* op);
 
 }  // namespace die

@@ -32,7 +32,7 @@ cudaEvent_t next_event() {
     }
     return g_pool[g_used++];
 }
-const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_fwd", "dots", "cgs_update_dots",
+const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_fwd", "dots", "dots32", "cgs_update_dots",
                                 "cgs_update_norm", "scale", "defl_update", "lincomb", "small_dense", "other"};
 }  // namespace
 

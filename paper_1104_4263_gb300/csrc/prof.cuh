@@ -12,7 +12,8 @@ enum ProfKernel {
     PK_COLS,              // K2: column FFT, Green-spectrum multiply, inverse column FFT
     PK_ROWS_INV,          // K3: row inverse FFT + crop + subtract
     PK_ROWS_INV_FWD,      // K3K1: fused row inverse of A(chi) and row forward of A(chi')
-    PK_DOTS,              // batched projections V^* w
+    PK_DOTS,              // batched projections V^* w (FP64 basis)
+    PK_DOTS32,            // batched projections with the complex64 deflation basis
     PK_UPDATE_DOTS,       // CGS2 sweep 2: w -= V h, projections again
     PK_UPDATE_NORM,       // CGS2 sweep 3: w -= V h, norm (+ Givens step)
     PK_SCALE,             // vector scaling

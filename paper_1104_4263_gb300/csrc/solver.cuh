@@ -17,6 +17,8 @@ struct SolverCache {
     double2* btil = nullptr;
     double2* tmp = nullptr;
     double2* z = nullptr;
+    float2* v32 = nullptr;      // complex64 copy of the current Arnoldi vector (FP32-inner + deflation)
+    float2* z32 = nullptr;      // complex64 P^-1 v of the FP32-inner form
     double2* small = nullptr;   // H, cs, sn, g, h1, h2, y, scalars
     double* hist = nullptr;
     int* ints = nullptr;        // done, k, flags
@@ -42,6 +44,7 @@ struct defl_s {
     long n = 0;
     int regularized = 0;
     double2* V = nullptr;       // r * n, vector i at V + i * n
+    float2* V32 = nullptr;      // complex64 copy of V (FP32-inner solves)
     double2* M = nullptr;       // r * r, column-major
     double2* s = nullptr;       // r projections (scratch)
     die::RedScratch rs;
@@ -51,4 +54,6 @@ struct defl_s {
 namespace die {
 // z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip` as for the Krylov kernels.
 die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st);
+// The same entirely in complex64 (copy of V, FP32 sums), for the FP32-inner solves.
+die_status defl_apply32(defl_s* d, const float2* x, float2* z, const int* skip, cudaStream_t st);
 }  // namespace die

@@ -36,7 +36,7 @@ class Desc(ct.Structure):
 
 class GmresOpts(ct.Structure):
     _fields_ = [("restart", ct.c_int), ("max_iters", ct.c_int), ("tol", ct.c_double), ("regularized", ct.c_int),
-                ("use_x0", ct.c_int), ("inner", ct.c_int), ("timing", ct.c_int)]
+                ("use_x0", ct.c_int), ("inner", ct.c_int), ("timing", ct.c_int), ("reorth_eta", ct.c_double)]
 
 
 class GmresReport(ct.Structure):
@@ -44,7 +44,7 @@ class GmresReport(ct.Structure):
                 ("rel_res_solved", ct.c_double), ("rel_res_orig", ct.c_double),
                 ("t_matvec", ct.c_double), ("t_orth", ct.c_double), ("t_defl", ct.c_double),
                 ("t_total", ct.c_double), ("history", ct.POINTER(ct.c_double)), ("history_cap", ct.c_int),
-                ("history_len", ct.c_int)]
+                ("history_len", ct.c_int), ("n_reorth", ct.c_int)]
 
 
 class DeflOpts(ct.Structure):
@@ -234,7 +234,8 @@ class Operator:
 
     def solve(self, b, x=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
               regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
-              timing: bool = False, history: int = 0, stream=None, raise_on_noconv: bool = False):
+              timing: bool = False, history: int = 0, stream=None, raise_on_noconv: bool = False,
+              reorth_eta: float = 0.0):
         """Restarted GMRES; returns (x, report dict).  x (complex128) may hold an initial guess."""
         import numpy as np
         import torch
@@ -243,7 +244,8 @@ class Operator:
         use_x0 = x is not None
         if x is None:
             x = torch.empty_like(b)
-        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, int(bool(timing)))
+        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, int(bool(timing)),
+                         float(reorth_eta))
         rep = GmresReport()
         hist = None
         if history > 0:
@@ -256,7 +258,8 @@ class Operator:
             raise DieError(code, "gmres_solve")
         out = {"status": STATUS[code], "converged": code == 0, "cycles": rep.cycles, "iters": rep.iters,
                "n_apply": rep.n_apply, "rel_res_solved": rep.rel_res_solved, "rel_res_orig": rep.rel_res_orig,
-               "t_matvec": rep.t_matvec, "t_orth": rep.t_orth, "t_defl": rep.t_defl, "t_total": rep.t_total}
+               "t_matvec": rep.t_matvec, "t_orth": rep.t_orth, "t_defl": rep.t_defl, "t_total": rep.t_total,
+               "n_reorth": rep.n_reorth}
         if hist is not None:
             out["history"] = hist[:rep.history_len].copy()
         return x, out

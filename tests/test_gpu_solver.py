@@ -31,7 +31,8 @@ def test_plain_gmres_config1(cyl32):
     op = die.Operator(p.eps_r, p.h)
     bt = op.plane_wave(0.0)
     assert np.max(np.abs(bt.cpu().numpy() - b)) < 1e-12
-    u, rep = op.solve(bt, restart=20, tol=1e-8, max_iters=20000, history=5000)
+    # classical DGKS threshold: orthogonality at working precision, like the oracle's MGS
+    u, rep = op.solve(bt, restart=20, tol=1e-8, max_iters=20000, history=5000, reorth_eta=2 ** -0.5)
     assert rep["converged"] and rep["rel_res_solved"] <= 1e-8
     kappa = np.linalg.cond(A)
     assert rel(u.cpu().numpy(), x) < 10 * kappa * 1e-8
@@ -43,6 +44,20 @@ def test_plain_gmres_config1(cyl32):
     assert np.max(np.abs(h[:20] - first) / first) < 1e-9
     # later cycles drift by rounding (CGS2 here, MGS in the oracle); totals stay close
     assert abs(rep["iters"] - ref.iters) <= 0.1 * ref.iters, (rep["iters"], ref.iters)
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.1, 1.0])
+def test_reorth_threshold_keeps_solution(cyl32, eta):
+    """Default (0.01), looser and always-on re-orthogonalisation all reach the direct solution."""
+    p, A, b, x = cyl32
+    op = die.Operator(p.eps_r, p.h)
+    u, rep = op.solve(op.plane_wave(0.0), restart=20, tol=1e-8, max_iters=20000, reorth_eta=eta)
+    assert rep["converged"] and rep["rel_res_solved"] <= 1e-8
+    assert rel(u.cpu().numpy(), x) < 10 * np.linalg.cond(A) * 1e-8
+    if eta >= 1.0:
+        assert rep["n_reorth"] == rep["iters"]
+    else:
+        assert rep["n_reorth"] < rep["iters"]
 
 
 def test_field_matches_cylinder_series(cyl32):
