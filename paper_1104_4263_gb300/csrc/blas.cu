@@ -419,9 +419,12 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.eta2 = eta2;
     DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st));
     DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st));
-    DIE_TRY(k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st));
-    DIE_TRY(k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, nullptr, rs, skip2, st));
-    return DIE_OK;
+    g_prof_override = PK_DOTS_REORTH;
+    die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st);
+    g_prof_override = PK_UPDATE_REORTH;
+    if (s == DIE_OK) s = k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, nullptr, rs, skip2, st);
+    g_prof_override = -1;
+    return s;
 }
 
 die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32) {

@@ -7,6 +7,7 @@
 namespace die {
 
 bool g_prof_on = false;
+int g_prof_override = -1;
 
 namespace {
 struct Rec {
@@ -32,8 +33,9 @@ cudaEvent_t next_event() {
     }
     return g_pool[g_used++];
 }
-const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_fwd", "dots", "dots32", "cgs_update_dots",
-                                "cgs_update_norm", "scale", "defl_update", "lincomb", "small_dense", "other"};
+const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_fwd", "dots", "dots32",
+                                "cgs_update_norm", "dots_reorth", "update_reorth", "scale",
+                                "defl_update", "lincomb", "small_dense", "other"};
 }  // namespace
 
 void prof_mark(int id, cudaStream_t st, int stop) {

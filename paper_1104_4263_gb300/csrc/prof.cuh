@@ -14,8 +14,9 @@ enum ProfKernel {
     PK_ROWS_INV_FWD,      // K3K1: fused row inverse of A(chi) and row forward of A(chi')
     PK_DOTS,              // batched projections V^* w (FP64 basis)
     PK_DOTS32,            // batched projections with the complex64 deflation basis
-    PK_UPDATE_DOTS,       // CGS2 sweep 2: w -= V h, projections again
-    PK_UPDATE_NORM,       // CGS2 sweep 3: w -= V h, norm (+ Givens step)
+    PK_UPDATE_NORM,       // Gram-Schmidt update w -= V h with the norm of the result
+    PK_DOTS_REORTH,       // second (re-orthogonalisation) pass: projections
+    PK_UPDATE_REORTH,     // second pass: update
     PK_SCALE,             // vector scaling
     PK_DEFL_UPDATE,       // deflation z = x + V (M s)
     PK_LINCOMB,           // x += V y
@@ -25,13 +26,15 @@ enum ProfKernel {
 };
 
 extern bool g_prof_on;
+extern int g_prof_override;      // >= 0: record launches under this class instead
 void prof_mark(int id, cudaStream_t st, int stop);
 
 }  // namespace die
 
-#define DIE_PROF(id, st, ...)                                  \
-    do {                                                       \
-        if (die::g_prof_on) die::prof_mark((id), (st), 0);     \
-        __VA_ARGS__;                                           \
-        if (die::g_prof_on) die::prof_mark((id), (st), 1);     \
+#define DIE_PROF(id, st, ...)                                                                    \
+    do {                                                                                         \
+        const int pid_ = die::g_prof_override >= 0 ? die::g_prof_override : (id);               \
+        if (die::g_prof_on) die::prof_mark(pid_, (st), 0);                                       \
+        __VA_ARGS__;                                                                             \
+        if (die::g_prof_on) die::prof_mark(pid_, (st), 1);                                       \
     } while (0)
