@@ -41,6 +41,7 @@ RESTART = 30
 R_DEFL = 20
 TOL = 1e-6
 STEP_ITERS = 1500
+PROF_STEPS = 2
 METRIC = "regularized DIE matvecs/s + GMRES solve time to 1e-6 residual vs plain FP64, %HBM roofline"
 UNIT = "regularized matvecs/s"
 WORKLOAD = ("core-shell 512x512 (eps -2+0.1i core R1.5, 20+0.5i shell R2.5, side 8): A_R A P^-1, GMRES(30), r=20, "
@@ -209,9 +210,14 @@ def main():
     ap.add_argument("--step-iters", type=int, default=STEP_ITERS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 and time-to-tol comparisons")
+    ap.add_argument("--profile-driver", action="store_true",
+                    help="short fixed run for ncu captures: one complex64 regularised product, then one "
+                         "30-step FP32-inner regularised GMRES cycle without and one with deflation (r=20)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_driver:
+        return profile_driver(args)
 
     import numpy as np
     import torch
@@ -252,7 +258,7 @@ def main():
     reps = []
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk, die.KernelTimer() as kt:
+    with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -263,6 +269,15 @@ def main():
     products_local = sum(r["iters"] for r in reps)
     products, dt = replicas.combine(products_local, dt_local, dist)
     value = products / dt
+    # per-kernel times: CUDA events around every library launch, in PROF_STEPS further
+    # steps identical to the timed ones (kept out of the timed region: the events add
+    # host work per launch)
+    prof_reps = []
+    with die.KernelTimer() as kt:
+        for _ in range(PROF_STEPS):
+            prof_reps.append(step()[1])
+    prof_products = sum(r["iters"] for r in prof_reps)
+    prof_cycles = sum(r["cycles"] for r in prof_reps)
 
     # end to end through the public API: pinned host b -> device, solve, x -> pinned host
     hb = b.cpu().pin_memory()
@@ -295,7 +310,8 @@ def main():
                       "parallelism": f"replicas x{world} (one incidence angle per GPU)", "l2": L2_NOTE}}
     out["e2e"] = {"value": e2e_units / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes}
-    out["gpu_launches"] = sum(v["launches"] for v in kt.result.values())
+    # library kernels per step (counted in the identical profiled steps) x timed steps
+    out["gpu_launches"] = int(round(sum(v["launches"] for v in kt.result.values()) / PROF_STEPS * args.steps))
     out["gmres"] = {"arnoldi_steps_per_step": last["iters"], "cycles": last["cycles"], "n_reorth": last["n_reorth"],
                     "rel_res_solved_after_step": last["rel_res_solved"], "rel_res_orig_after_step": last["rel_res_orig"],
                     "reached_tol": last["converged"], "tol": TOL, "step_s": dt / args.steps,
@@ -309,13 +325,13 @@ def main():
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    cycles = sum(r["cycles"] for r in reps)
+    cycles = prof_cycles
     fp64_products = cycles                 # one FP64 restart residual per cycle (x0 = 0 skips the first)
-    kernels = {}
+    kernels = {"_note": f"CUDA events around each launch over {PROF_STEPS} extra steps identical to the timed ones"}
     best = None
     for cls, st in kt.result.items():
         ent = {"launches": st["launches"], "ms": round(st["ms"], 3)}
-        bound, work = work_model(cls, p, op, D.r, RESTART, cycles, products_local, fp64_products)
+        bound, work = work_model(cls, p, op, D.r, RESTART, cycles, prof_products, fp64_products)
         if bound == "hbm":
             ent.update({"bound": "hbm", "GBps": work / (st["ms"] / 1e3) / 1e9})
             ent["frac"] = ent["GBps"] / hbm_peak
@@ -328,7 +344,7 @@ def main():
     out["kernels"] = kernels
     if best:
         k = kernels[best]
-        bound, work = work_model(best, p, op, D.r, RESTART, cycles, products_local, fp64_products)
+        bound, work = work_model(best, p, op, D.r, RESTART, cycles, prof_products, fp64_products)
         per_launch = work / k["launches"]
         avg_s = k["ms"] / k["launches"] / 1e3
         if bound == "hbm":
@@ -355,6 +371,27 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def profile_driver(args):
+    """Fixed short run on the 512^2 core-shell for kernel captures (launch order: the
+    complex64 product's K1 K2 K3K1 K2 K3, then GMRES kernels without, then with deflation)."""
+    import torch
+
+    from paper_1104_4263_gb300 import die, workloads as W
+    p = W.config2(args.n)
+    op32 = die.Operator(p.eps_r, p.h, prec=die.DIE_FP32_INNER)
+    x = torch.ones(2, p.n2, p.n1, dtype=torch.complex64, device="cuda")
+    op32.apply_regularized(x)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    _, r1 = op.solve(b, restart=RESTART, tol=TOL, max_iters=RESTART, regularized=True, inner=die.DIE_FP32_INNER)
+    D = die.Deflation(op, R_DEFL, tol=1e-4, regularized=True, inner=die.DIE_FP32_INNER)
+    _, r2 = op.solve(b, restart=RESTART, tol=TOL, max_iters=RESTART, regularized=True, inner=die.DIE_FP32_INNER,
+                     deflation=D)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_driver": "ok", "steps": [r1["iters"], r2["iters"]]}))
     return 0
 
 

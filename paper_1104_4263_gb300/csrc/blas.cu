@@ -1,9 +1,10 @@
 // Krylov-space kernels (see krylov.cuh).
 //
 // Projections: each block owns a contiguous slice of the rows; each warp accumulates
-// whole vectors over that slice (lanes stride the rows, so basis reads are coalesced,
-// w is re-read from L1, and there is no barrier or reduction until the end), then one
-// warp reduction per vector gives the block's partial.  The last block to arrive
+// whole vectors over that slice (lanes stride the rows in batches of loads, so basis
+// reads are coalesced and many are in flight; w is re-read from L1; there is no
+// barrier or reduction until the end), then one warp reduction per vector gives the
+// block's partial (stride = the launch's block count).  The last block to arrive
 // (atomic counter) sums the partials of each vector in a fixed order, so results do
 // not depend on scheduling.  Updates: one thread per row, sum over the basis with
 // fused multiply-adds (4 per complex term); the optional norm uses the same
@@ -17,6 +18,11 @@ namespace die {
 template <typename V> struct acc_of;
 template <> struct acc_of<double2> { using type = double; };
 template <> struct acc_of<float2> { using type = float; };
+
+// Fused multiply-add in the operands' own precision (a bare fma() on floats would be
+// promoted to the FP64 pipe, which is narrow on GB300).
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -41,7 +47,7 @@ __device__ __forceinline__ void final_sums(const double2* partial, int nv, doubl
     for (int i = warp; i < nv; i += nw) {
         double sx = 0, sy = 0;
         for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const double2 p = __ldcg(&partial[(long)i * kRedBlocks + b]);
+            const double2 p = __ldcg(&partial[(long)i * gridDim.x + b]);
             sx += p.x;
             sy += p.y;
         }
@@ -78,16 +84,16 @@ __global__ void __launch_bounds__(kRedThreads) dots_kernel(const VT* __restrict_
                 for (int u = 0; u < U; u++) { a[u] = p[idx + 32 * u]; b[u] = w[idx + 32 * u]; }
 #pragma unroll
                 for (int u = 0; u < U; u += 2) {
-                    ax = fma(a[u].x, b[u].x, ax); ax = fma(a[u].y, b[u].y, ax);
-                    ay = fma(a[u].x, b[u].y, ay); ay = fma(-a[u].y, b[u].x, ay);
-                    bx = fma(a[u + 1].x, b[u + 1].x, bx); bx = fma(a[u + 1].y, b[u + 1].y, bx);
-                    by = fma(a[u + 1].x, b[u + 1].y, by); by = fma(-a[u + 1].y, b[u + 1].x, by);
+                    ax = fmac(a[u].x, b[u].x, ax); ax = fmac(a[u].y, b[u].y, ax);
+                    ay = fmac(a[u].x, b[u].y, ay); ay = fmac(-a[u].y, b[u].x, ay);
+                    bx = fmac(a[u + 1].x, b[u + 1].x, bx); bx = fmac(a[u + 1].y, b[u + 1].y, bx);
+                    by = fmac(a[u + 1].x, b[u + 1].y, by); by = fmac(-a[u + 1].y, b[u + 1].x, by);
                 }
             }
             for (; idx < r1; idx += 32) {
                 const VT a = p[idx], b = w[idx];
-                ax = fma(a.x, b.x, ax); ax = fma(a.y, b.y, ax);
-                ay = fma(a.x, b.y, ay); ay = fma(-a.y, b.x, ay);
+                ax = fmac(a.x, b.x, ax); ax = fmac(a.y, b.y, ax);
+                ay = fmac(a.x, b.y, ay); ay = fmac(-a.y, b.x, ay);
             }
         } else {                                            // the norm of w
             for (; idx + 32 * (U - 1) < r1; idx += 32 * U) {
@@ -95,18 +101,18 @@ __global__ void __launch_bounds__(kRedThreads) dots_kernel(const VT* __restrict_
 #pragma unroll
                 for (int u = 0; u < U; u++) b[u] = w[idx + 32 * u];
 #pragma unroll
-                for (int u = 0; u < U; u++) { ax = fma(b[u].x, b[u].x, ax); bx = fma(b[u].y, b[u].y, bx); }
+                for (int u = 0; u < U; u++) { ax = fmac(b[u].x, b[u].x, ax); bx = fmac(b[u].y, b[u].y, bx); }
             }
             for (; idx < r1; idx += 32) {
                 const VT b = w[idx];
-                ax = fma(b.x, b.x, ax);
-                bx = fma(b.y, b.y, bx);
+                ax = fmac(b.x, b.x, ax);
+                bx = fmac(b.y, b.y, bx);
             }
             ax += bx;
             bx = 0;
         }
         const double sx = warp_sum_d((double)ax + (double)bx), sy = warp_sum_d((double)ay + (double)by);
-        if (lane == 0) rs.partial[(long)i * kRedBlocks + blockIdx.x] = make_double2(sx, sy);
+        if (lane == 0) rs.partial[(long)i * gridDim.x + blockIdx.x] = make_double2(sx, sy);
     }
     if (arrive_last(rs.counter)) {
         final_sums(rs.partial, nvt, out);
@@ -114,24 +120,33 @@ __global__ void __launch_bounds__(kRedThreads) dots_kernel(const VT* __restrict_
     }
 }
 
-// z = x + V c with c = M s (rounded to FP32), all complex64: the deflation update of
-// the FP32-inner solves.  Each block forms c redundantly.
+// c = M s (r x r times r, FP64 sums) rounded to complex64; one warp per coefficient.
+__global__ void defl_coef_kernel(const double2* __restrict__ M, const double2* __restrict__ s, int r, float2* cf,
+                                 const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < r; i += nw) {
+        double cx = 0, cy = 0;
+        for (int q = lane; q < r; q += 32) {
+            const double2 m = M[(long)q * r + i], sv = s[q];
+            cx = fmac(m.x, sv.x, cx); cx = fmac(-m.y, sv.y, cx);
+            cy = fmac(m.x, sv.y, cy); cy = fmac(m.y, sv.x, cy);
+        }
+        cx = warp_sum_d(cx);
+        cy = warp_sum_d(cy);
+        if (lane == 0) cf[i] = make_float2((float)cx, (float)cy);
+    }
+}
+
+// z = x + V c (c precomputed, complex64), all complex64: the deflation update of the
+// FP32-inner solves.
 __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2* __restrict__ V, long ldv, int r,
-                                                                    const double2* __restrict__ M,
-                                                                    const double2* __restrict__ s,
+                                                                    const float2* __restrict__ cf,
                                                                     const float2* x, float2* z, long n,
                                                                     const int* skip) {
     if (skip && *skip) return;
     __shared__ float2 cs[kMaxBasis];
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-        double cx = 0, cy = 0;
-        for (int q = 0; q < r; q++) {
-            const double2 m = M[(long)q * r + i], sv = s[q];
-            cx = fma(m.x, sv.x, cx); cx = fma(-m.y, sv.y, cx);
-            cy = fma(m.x, sv.y, cy); cy = fma(m.y, sv.x, cy);
-        }
-        cs[i] = make_float2((float)cx, (float)cy);
-    }
+    for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = cf[i];
     __syncthreads();
     const long stride = (long)gridDim.x * blockDim.x;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -172,8 +187,8 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
         if (M) {
             for (int q = 0; q < k; q++) {
                 const double2 m = M[(long)q * k + i], sv = s[q];
-                cx = fma(m.x, sv.x, cx); cx = fma(-m.y, sv.y, cx);
-                cy = fma(m.x, sv.y, cy); cy = fma(m.y, sv.x, cy);
+                cx = fmac(m.x, sv.x, cx); cx = fmac(-m.y, sv.y, cx);
+                cy = fmac(m.x, sv.y, cy); cy = fmac(m.y, sv.x, cy);
             }
         } else {
             cx = sign * coef[i].x;
@@ -194,20 +209,20 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
         for (; i + 1 < k; i += 2) {
             const VT a = V[(long)i * ldv + idx], c = cs[i];
             const VT b = V[(long)(i + 1) * ldv + idx], d = cs[i + 1];
-            x0 = fma(a.x, c.x, x0); x0 = fma(-a.y, c.y, x0);
-            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
-            x1 = fma(b.x, d.x, x1); x1 = fma(-b.y, d.y, x1);
-            y1 = fma(b.x, d.y, y1); y1 = fma(b.y, d.x, y1);
+            x0 = fmac(a.x, c.x, x0); x0 = fmac(-a.y, c.y, x0);
+            y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
+            x1 = fmac(b.x, d.x, x1); x1 = fmac(-b.y, d.y, x1);
+            y1 = fmac(b.x, d.y, y1); y1 = fmac(b.y, d.x, y1);
         }
         if (i < k) {
             const VT a = V[(long)i * ldv + idx], c = cs[i];
-            x0 = fma(a.x, c.x, x0); x0 = fma(-a.y, c.y, x0);
-            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+            x0 = fmac(a.x, c.x, x0); x0 = fmac(-a.y, c.y, x0);
+            y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
         }
         double2 o = make_double2((double)x0 + (double)x1, (double)y0 + (double)y1);
         if (base) { const double2 bv = base[idx]; o.x += bv.x; o.y += bv.y; }
         out[idx] = o;
-        if (NORM) { nacc = fma(o.x, o.x, nacc); nacc = fma(o.y, o.y, nacc); }
+        if (NORM) { nacc = fmac(o.x, o.x, nacc); nacc = fmac(o.y, o.y, nacc); }
     }
     if (NORM) {
         __shared__ double red[kRedThreads / 32];
@@ -400,10 +415,11 @@ die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, co
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, const float2* x,
-                           float2* z, long n, const int* skip, cudaStream_t st) {
+die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, float2* cf,
+                           const float2* x, float2* z, long n, const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, defl_update32_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, M, s, x, z, n, skip));
+    DIE_PROF(PK_SMALL, st, defl_coef_kernel<<<1, 256, 0, st>>>(M, s, r, cf, skip));
+    DIE_PROF(PK_DEFL_UPDATE, st, defl_update32_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, cf, x, z, n, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

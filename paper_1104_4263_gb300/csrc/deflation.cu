@@ -125,6 +125,7 @@ static void free_defl(defl_s* d) {
     if (d->V) cudaFree(d->V);
     if (d->M) cudaFree(d->M);
     if (d->V32) cudaFree(d->V32);
+    if (d->c32) cudaFree(d->c32);
     if (d->s) cudaFree(d->s);
     free_red_scratch(&d->rs);
     delete d;
@@ -281,6 +282,7 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
         DIE_TRY(k_dots(d->V, n, r, AV, n, 0, d->M + (long)l * r, rs, nullptr, st));
     }
     DIE_TRY(dalloc((void**)&d->V32, (size_t)r * n * sizeof(float2)));
+    DIE_TRY(dalloc((void**)&d->c32, (size_t)r * sizeof(float2)));
     DIE_TRY(k_to_c64(d->V, d->V32, (long)r * n, st));
     inverse_minus_identity_kernel<<<1, 32, 0, st>>>(d->M, r, w.ist + 4, w.ist);
     DIE_LAUNCH_CHECK();

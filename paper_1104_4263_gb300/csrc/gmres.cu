@@ -56,6 +56,9 @@ void free_solver_cache(dieop_s* op) {
     free_red_scratch(&c->rs);
     if (c->host) cudaFreeHost(c->host);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->join)
+        if (e) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     op->solver = nullptr;
 }
@@ -96,6 +99,8 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     }
     const double2 one = make_double2(1.0, 0.0);
     DIE_CUDA_TRY(cudaMemcpy(c->one, &one, sizeof one, cudaMemcpyHostToDevice));
+    DIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    for (auto& e : c->join) DIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->ev.resize(4 * (size_t)(m + 1));
     for (auto& e : c->ev) DIE_CUDA_TRY(cudaEventCreate(&e));
     return DIE_OK;
@@ -109,7 +114,7 @@ die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, 
 
 die_status defl_apply32(defl_s* d, const float2* x, float2* z, const int* skip, cudaStream_t st) {
     DIE_TRY(k_dots32(d->V32, d->n, d->r, x, d->n, d->s, d->rs, skip, st));
-    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
+    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->M, d->s, d->c32, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
@@ -137,6 +142,50 @@ static die_status norm2_host(SolverCache* c, const double2* v, long n, double2* 
     return DIE_OK;
 }
 
+// Keeps a buffer resident in L2 while a solve runs: a persisting access-policy window
+// on the solve's stream (a per-context reservation, released and restored on exit).
+// Best effort: any refusal leaves caching as it was.
+struct L2Pin {
+    cudaStream_t st = nullptr;
+    bool on = false;
+    size_t old_limit = 0;
+    L2Pin(cudaStream_t s, const void* base, size_t bytes) : st(s) {
+        int dev = 0, max_persist = 0, max_window = 0;
+        if (!base || bytes == 0 || cudaGetDevice(&dev) != cudaSuccess) return;
+        if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
+            max_persist <= 0 || max_window <= 0) {
+            cudaGetLastError();
+            return;
+        }
+        if (cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) { cudaGetLastError(); return; }
+        const size_t win = bytes < (size_t)max_window ? bytes : (size_t)max_window;
+        const size_t res = win < (size_t)max_persist ? win : (size_t)max_persist;
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, res) != cudaSuccess) { cudaGetLastError(); return; }
+        cudaStreamAttrValue a = {};
+        a.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+        a.accessPolicyWindow.num_bytes = win;
+        a.accessPolicyWindow.hitRatio = (float)((double)res / (double)win);
+        a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        if (cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &a) != cudaSuccess) {
+            cudaGetLastError();
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+            return;
+        }
+        on = true;
+    }
+    ~L2Pin() {
+        if (!on) return;
+        cudaStreamAttrValue a = {};
+        a.accessPolicyWindow.num_bytes = 0;
+        cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &a);
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+        cudaGetLastError();
+    }
+};
+
 static double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -152,7 +201,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return DIE_EINVAL;
     if (defl && (defl->op_id != op->id || defl->regularized != (o->regularized ? 1 : 0))) return DIE_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t ust = (cudaStream_t)stream;
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
     const double eta = o->reorth_eta > 0 ? o->reorth_eta : 0.01;
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
@@ -161,6 +210,17 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     const int hist_cap = o->max_iters < (1 << 22) ? (o->max_iters > 0 ? o->max_iters : 1) : (1 << 22);
     DIE_TRY(ensure_solver_cache(op, m, hist_cap));
     SolverCache* c = solver_cache(op);
+    // The solve runs on the library's own stream, ordered after the caller's stream at
+    // entry and before it at every exit (a stream of its own can carry the L2
+    // access-policy window below, which the legacy default stream cannot).
+    cudaStream_t st = c->stream;
+    DIE_CUDA_TRY(cudaEventRecord(c->join[0], ust));
+    DIE_CUDA_TRY(cudaStreamWaitEvent(st, c->join[0], 0));
+    struct Join {
+        cudaStream_t from, to;
+        cudaEvent_t ev;
+        ~Join() { if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0); }
+    } join{st, ust, c->join[1]};
     const double2* b = (const double2*)b_;
     double2* x = (double2*)x_;
 
@@ -214,6 +274,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     // normalising kernel keeps a complex64 copy of the current Arnoldi vector.
     const bool defl32 = defl && mixed;
     float2* v32 = defl32 ? c->v32 : nullptr;
+    // the complex64 deflation basis is read twice per Arnoldi step: keep it in L2
+    L2Pin pin(st, defl32 ? defl->V32 : nullptr, defl32 ? (size_t)defl->r * n * sizeof(float2) : 0);
     if (bnorm == 0.0) {
         DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
         status = DIE_OK;
@@ -306,7 +368,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         rel_orig = b2 > 0 ? sqrt(r2 / b2) : 0.0;
     }
     int nre = 0;
-    DIE_CUDA_TRY(cudaMemcpy(&nre, S.nreorth, sizeof(int), cudaMemcpyDeviceToHost));
+    DIE_CUDA_TRY(cudaMemcpyAsync(&nre, S.nreorth, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DIE_CUDA_TRY(cudaStreamSynchronize(st));
     if (rep) {
         rep->cycles = cycles;
         rep->iters = iters;

@@ -69,9 +69,10 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
 // z = x + V (M s); M r x r column-major; s the projections V^* x.  z may equal x.
 die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
                          double2* z, long n, const int* skip, cudaStream_t st);
-// All-complex64 deflation update (FP32-inner solves): z = x + V (M s).
-die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, const float2* x,
-                           float2* z, long n, const int* skip, cudaStream_t st);
+// All-complex64 deflation update (FP32-inner solves): cf = M s (rounded, r entries of
+// device scratch), then z = x + V cf.
+die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, float2* cf,
+                           const float2* x, float2* z, long n, const int* skip, cudaStream_t st);
 
 // Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion:
 // h1 = V^* w (||w||^2 in h1[nv]); w -= V h1 (||w||^2 -> nrm[0]); if ||w||^2 < eta2

@@ -27,6 +27,8 @@ struct SolverCache {
     RedScratch rs;
     double* host = nullptr;     // pinned readback area
     std::vector<cudaEvent_t> ev;
+    cudaStream_t stream = nullptr;  // internal stream of the solves (joined to the caller's)
+    cudaEvent_t join[2] = {nullptr, nullptr};
 };
 
 void free_solver_cache(dieop_s* op);
@@ -45,6 +47,7 @@ struct defl_s {
     int regularized = 0;
     double2* V = nullptr;       // r * n, vector i at V + i * n
     float2* V32 = nullptr;      // complex64 copy of V (FP32-inner solves)
+    float2* c32 = nullptr;      // r coefficients M (V^* x), complex64 (scratch)
     double2* M = nullptr;       // r * r, column-major
     double2* s = nullptr;       // r projections (scratch)
     die::RedScratch rs;
