@@ -63,7 +63,7 @@ typedef struct defl_s* defl_t;
 /* Operator description (Section 4: uniform grid of step h; units of the
  * background wavelength, so k_b = 2 pi by default). */
 typedef struct dieop_desc {
-    int n1, n2;            /* cells along x1 / x2; 2 <= n <= 4096                              */
+    int n1, n2;            /* cells along x1 / x2; 2 <= n <= 2048                              */
     double h;              /* cell side in background wavelengths, > 0                         */
     double k_b;            /* background wavenumber; <= 0 selects 2 pi                         */
     die_precision prec;    /* element type of dieop_apply / dieop_apply_regularized I/O        */
@@ -183,14 +183,14 @@ die_status deflation_apply(defl_t defl, const void* x, void* z, void* stream);
  * for example a solver embedded in another program that has already handed all
  * device memory to its own pool allocator, or a latency-critical loop where the
  * device-wide synchronisation that cudaMalloc and cudaFree can cause is not
- * acceptable.  Its scratch (projections, per-block partial sums and a reduction
- * counter, about 625 KB) is a static device array inside the library that every GPU
- * loading the library keeps until the process exits.
+ * acceptable.  Its scratch (projections, per-block and per-group partial sums and the
+ * reduction's arrival counters, about 650 KB) is a static device array inside the
+ * library that every GPU loading the library keeps until the process exits.
  *   - defl must have r <= 128, else DIE_EINVAL; x, z as for deflation_apply.
  *   - The first call on a device looks up the array's address on that device (call
  *     it with that device current); make this first call before any stream capture.
  *   - All calls share the one array (it keeps the last call's contents; the counter
- *     is cleared at the start of each call): calls that overlap on the GPU, e.g. on
+ *     are cleared at the start of each call): calls that overlap on the GPU, e.g. on
  *     two streams at once, race and give wrong results.  Serialise them. */
 die_status deflation_apply_noalloc(defl_t defl, const void* x, void* z, void* stream);
 

@@ -1,15 +1,16 @@
 // Krylov-space kernels (see krylov.cuh).
 //
-// Projections: each block owns a contiguous slice of the rows; each warp accumulates
-// whole vectors over that slice (lanes stride the rows in batches of loads, so basis
-// reads are coalesced and many are in flight; w is re-read from L1; there is no
-// barrier or reduction until the end), then one warp reduction per vector gives the
-// block's partial (stride = the launch's block count).  The last block to arrive
-// (atomic counter) sums the partials of each vector in a fixed order, so results do
-// not depend on scheduling.  Updates: one thread per row, sum over the basis with
-// fused multiply-adds (4 per complex term); the optional norm uses the same
-// deterministic two-level reduction.  Every complex multiply-add is written as four
-// FMAs: on GB300 the FP64 pipe (about 2 FMA per clock per SM) bounds these kernels.
+// Projections: one thread per row (grid-stride), holding the row of w in registers and
+// the running sums of a group of basis vectors; the loads of a group are issued
+// together, so many are in flight.  At the end of a group every warp sums its lanes by
+// recursive halving (each level exchanges half as many values as the one before), the
+// eight warp sums of each value are added in a fixed order, and the block writes one
+// partial per vector.  The partials are summed in two levels (groups of kRedGroup
+// blocks, then the groups) by the last block to arrive at each level, in block and
+// group order, so results do not depend on scheduling.  Updates: one thread per row,
+// sum over the basis with fused multiply-adds (4 per complex term); the optional norm
+// uses the same two-level reduction.  Every complex multiply-add is written as four
+// FMAs: on GB300 the FP64 pipe (about 2 FMA per clock per SM) bounds the FP64 kernels.
 #include "krylov.cuh"
 #include "prof.cuh"
 
@@ -30,111 +31,243 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// True in exactly one block: the last one to finish writing its partials.
-__device__ __forceinline__ bool arrive_last(unsigned* counter) {
-    __shared__ int is_last;
+// Warp sums of K = 2^P values per lane by recursive halving: at offset o = 16, 8, ...
+// a lane keeps the half of its current values selected by (lane & o) and adds the
+// partner's copy of that half.  Afterwards lane l holds in v[0 .. C) (C = max(K/32, 1))
+// the 32-lane sums of the values with index (l >> (5 - H)) * C + c, H = min(P, 5).
+template <typename A, int K>
+__device__ __forceinline__ void warp_halving_sum(A (&v)[K]) {
+    static_assert(K >= 1 && K <= 64 && (K & (K - 1)) == 0, "K must be a power of two <= 64");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int lvl = 0; lvl < 5; lvl++) {
+        const int o = 16 >> lvl;
+        const int c = K >> lvl;
+        if (c >= 2) {
+            const int h = c >> 1;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < h; i++) {
+                const A send = up ? v[i] : v[i + h];
+                const A keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+}
+
+template <int K> __host__ __device__ constexpr int halving_levels() { return K >= 32 ? 5 : (K >= 16 ? 4 : (K >= 8 ? 3 : (K >= 4 ? 2 : (K >= 2 ? 1 : 0)))); }
+
+// Block partials of one group of CNT vectors: acc[2 v + c] is component c (0: re, 1: im)
+// of the running sum of vector g0 + v (entries from 2 CNT on are zero padding up to the
+// power of two K).  Writes partial[(g0 + v) * gridDim.x + blockIdx.x] for v < CNT.
+// red: K values per warp of shared memory.
+template <typename A, int K, int CNT>
+__device__ __forceinline__ void block_partials(A (&acc)[K], A* red, int g0, const RedScratch& rs) {
+    constexpr int H = halving_levels<K>();
+    constexpr int C = K >= 32 ? K / 32 : 1;
+    warp_halving_sum<A, K>(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if ((lane & ((1 << (5 - H)) - 1)) == 0) {
+#pragma unroll
+        for (int c = 0; c < C; c++) red[warp * K + (lane >> (5 - H)) * C + c] = acc[c];
+    }
+    __syncthreads();
+    double* pp = reinterpret_cast<double*>(rs.partial);
+    for (int e = threadIdx.x; e < 2 * CNT; e += blockDim.x) {
+        A s = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) s += red[q * K + e];
+        pp[2 * ((long)(g0 + (e >> 1)) * gridDim.x + blockIdx.x) + (e & 1)] = (double)s;
+    }
+    __syncthreads();
+}
+
+// Final sums of the per-block partials partial[i * gridDim.x + b], i < nv (see
+// RedScratch).  Every thread of every block calls it after its block's partials are
+// written; it returns true in the one block that has written out[0 .. nv), whose
+// threads may then read out.
+__device__ bool reduce_partials(const RedScratch& rs, int nv, double2* out) {
+    __shared__ int s_last;
+    const int G = gridDim.x, ng = (G + kRedGroup - 1) / kRedGroup, g = blockIdx.x / kRedGroup;
+    const int gsz = min(kRedGroup, G - g * kRedGroup);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) {
+        const bool last = atomicAdd(&rs.counter[1 + g], 1u) == (unsigned)(gsz - 1);
+        if (last) rs.counter[1 + g] = 0;
+        s_last = last;
+    }
     __syncthreads();
-    if (is_last) __threadfence();
-    return is_last;
-}
-
-// out[i] = sum over blocks of partial[i][b], i < nv (one warp per vector, fixed order).
-__device__ __forceinline__ void final_sums(const double2* partial, int nv, double2* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < nv; i += nw) {
-        double sx = 0, sy = 0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const double2 p = __ldcg(&partial[(long)i * gridDim.x + b]);
-            sx += p.x;
-            sy += p.y;
-        }
-        sx = warp_sum_d(sx);
-        sy = warp_sum_d(sy);
-        if (lane == 0) out[i] = make_double2(sx, sy);
+    if (!s_last) return false;
+    __threadfence();
+    const double* pp = reinterpret_cast<const double*>(rs.partial);
+    double* p2 = reinterpret_cast<double*>(rs.partial2);
+    for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {   // e = 2 i + component
+        const double* src = pp + 2 * ((long)(e >> 1) * G + (long)g * kRedGroup) + (e & 1);
+        double s = 0;
+        for (int b = 0; b < gsz; b++) s += __ldcg(src + 2 * b);
+        p2[2 * ((long)(e >> 1) * ng + g) + (e & 1)] = s;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool last = atomicAdd(&rs.counter[0], 1u) == (unsigned)(ng - 1);
+        if (last) rs.counter[0] = 0;
+        s_last = last;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double* o = reinterpret_cast<double*>(out);
+    for (int e = threadIdx.x; e < 2 * nv; e += blockDim.x) {
+        const double* src = p2 + 2 * (long)(e >> 1) * ng + (e & 1);
+        double s = 0;
+        for (int q = 0; q < ng; q++) s += __ldcg(src + 2 * q);
+        o[e] = s;
+    }
+    __syncthreads();
+    return true;
 }
 
-// Rows loaded per batch by each lane: enough independent loads in flight to cover
-// HBM latency with two blocks of eight warps per SM.
-template <typename VT> constexpr int dot_batch() { return sizeof(VT) == 8 ? 8 : 4; }
+// A block that skips its work still writes (zero) partials and takes part in the final
+// sums when the skip flag is "live": a flag that another stream may set while the
+// kernel runs, so that blocks of one launch may disagree on it.
+__device__ __forceinline__ void zero_partials(int g0, int K, int nvt, const RedScratch& rs) {
+    double* pp = reinterpret_cast<double*>(rs.partial);
+    for (int e = threadIdx.x; e < K; e += blockDim.x)
+        if (g0 + (e >> 1) < nvt) pp[2 * ((long)(g0 + (e >> 1)) * gridDim.x + blockIdx.x) + (e & 1)] = 0.0;
+}
 
-// out[i] = sum_e conj(V_i[e]) w[e]; w has the basis' element type (no conversions).
-// Warp q of a block handles vectors q, q+8, q+16, ... one at a time over the block's rows.
-template <typename VT>
-__global__ void __launch_bounds__(kRedThreads) dots_kernel(const VT* __restrict__ V, long ldv, int nv,
-                                                           const VT* __restrict__ w, long n, int with_norm,
-                                                           double2* out, RedScratch rs, const int* skip) {
+// conj(a) b accumulated into acc[0] (re), acc[1] (im)
+template <typename VT, typename A>
+__device__ __forceinline__ void conj_mac(const VT& a, const VT& b, A& re, A& im) {
+    re = fmac(a.x, b.x, re); re = fmac(a.y, b.y, re);
+    im = fmac(a.x, b.y, im); im = fmac(-a.y, b.x, im);
+}
+
+template <int X> __host__ __device__ constexpr int pow2ceil() { return X <= 1 ? 1 : 2 * pow2ceil<(X + 1) / 2>(); }
+
+// One group of CNT projections over this thread's rows (grid-stride), summed into the
+// block's partials.  Projection g0 + v is onto V_{g0+v}, or onto the vector itself for
+// index nv (the norm).  The basis loads of a row are issued first, then the row of the
+// vector: b = xin[idx], or (SCALE) w[idx] *= sc written back and b = its complex64
+// copy, also stored to xout.  CNT is a compile-time count: no predicated-off FMAs,
+// which would still occupy the FP64 pipe.
+template <typename VT, int CNT, bool SCALE>
+__device__ __forceinline__ void proj_group(const VT* __restrict__ V, long ldv, int g0, int nv, const VT* xin,
+                                           VT* xout, double2* w, double sc, long n,
+                                           typename acc_of<VT>::type* red, const RedScratch& rs) {
     using A = typename acc_of<VT>::type;
-    constexpr int U = dot_batch<VT>();
-    if (skip && *skip) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long r0 = n * (long)blockIdx.x / gridDim.x, r1 = n * (long)(blockIdx.x + 1) / gridDim.x;
-    const int nvt = nv + (with_norm ? 1 : 0);
-    for (int i = warp; i < nvt; i += 8) {
-        A ax = 0, ay = 0, bx = 0, by = 0;
-        long idx = r0 + lane;
-        if (i < nv) {
-            const VT* p = V + (long)i * ldv;
-            for (; idx + 32 * (U - 1) < r1; idx += 32 * U) {
-                VT a[U], b[U];
+    constexpr int K = pow2ceil<2 * CNT>();
+    // FP64: the a.y b.x terms of the imaginary parts go to their own sums, subtracted at
+    // the end, so that every step is a plain FMA (a negated operand costs an extra
+    // instruction on the FP64 pipe).
+    constexpr bool kSplit = sizeof(A) == 8;
+    A acc[K], accn[kSplit ? CNT : 1];
 #pragma unroll
-                for (int u = 0; u < U; u++) { a[u] = p[idx + 32 * u]; b[u] = w[idx + 32 * u]; }
+    for (int k = 0; k < K; k++) acc[k] = 0;
 #pragma unroll
-                for (int u = 0; u < U; u += 2) {
-                    ax = fmac(a[u].x, b[u].x, ax); ax = fmac(a[u].y, b[u].y, ax);
-                    ay = fmac(a[u].x, b[u].y, ay); ay = fmac(-a[u].y, b[u].x, ay);
-                    bx = fmac(a[u + 1].x, b[u + 1].x, bx); bx = fmac(a[u + 1].y, b[u + 1].y, bx);
-                    by = fmac(a[u + 1].x, b[u + 1].y, by); by = fmac(-a[u + 1].y, b[u + 1].x, by);
-                }
-            }
-            for (; idx < r1; idx += 32) {
-                const VT a = p[idx], b = w[idx];
-                ax = fmac(a.x, b.x, ax); ax = fmac(a.y, b.y, ax);
-                ay = fmac(a.x, b.y, ay); ay = fmac(-a.y, b.x, ay);
-            }
-        } else {                                            // the norm of w
-            for (; idx + 32 * (U - 1) < r1; idx += 32 * U) {
-                VT b[U];
+    for (int v = 0; v < (kSplit ? CNT : 1); v++) accn[v] = 0;
+    const VT* src[CNT];
 #pragma unroll
-                for (int u = 0; u < U; u++) b[u] = w[idx + 32 * u];
+    for (int v = 0; v < CNT; v++) src[v] = g0 + v < nv ? V + (long)(g0 + v) * ldv : xin;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        VT a[CNT];
 #pragma unroll
-                for (int u = 0; u < U; u++) { ax = fmac(b[u].x, b[u].x, ax); bx = fmac(b[u].y, b[u].y, bx); }
-            }
-            for (; idx < r1; idx += 32) {
-                const VT b = w[idx];
-                ax = fmac(b.x, b.x, ax);
-                bx = fmac(b.y, b.y, bx);
-            }
-            ax += bx;
-            bx = 0;
+        for (int v = 0; v < CNT; v++) a[v] = src[v][idx];
+        VT b;
+        if constexpr (SCALE) {
+            double2 u = w[idx];
+            u.x *= sc;
+            u.y *= sc;
+            w[idx] = u;
+            b.x = (A)u.x;
+            b.y = (A)u.y;
+            xout[idx] = b;
+        } else {
+            b = xin[idx];
         }
-        const double sx = warp_sum_d((double)ax + (double)bx), sy = warp_sum_d((double)ay + (double)by);
-        if (lane == 0) rs.partial[(long)i * gridDim.x + blockIdx.x] = make_double2(sx, sy);
+#pragma unroll
+        for (int v = 0; v < CNT; v++) {
+            if constexpr (kSplit) {
+                acc[2 * v] = fmac(a[v].x, b.x, acc[2 * v]);
+                acc[2 * v] = fmac(a[v].y, b.y, acc[2 * v]);
+                acc[2 * v + 1] = fmac(a[v].x, b.y, acc[2 * v + 1]);
+                accn[v] = fmac(a[v].y, b.x, accn[v]);
+            } else {
+                conj_mac(a[v], b, acc[2 * v], acc[2 * v + 1]);
+            }
+        }
     }
-    if (arrive_last(rs.counter)) {
-        final_sums(rs.partial, nvt, out);
-        if (threadIdx.x == 0) *rs.counter = 0;
+    if constexpr (kSplit) {
+#pragma unroll
+        for (int v = 0; v < CNT; v++) acc[2 * v + 1] -= accn[v];
     }
+    block_partials<A, K, CNT>(acc, red, g0, rs);
 }
 
-// c = M s (r x r times r, FP64 sums) rounded to complex64; one warp per coefficient.
-__global__ void defl_coef_kernel(const double2* __restrict__ M, const double2* __restrict__ s, int r, float2* cf,
-                                 const int* skip) {
-    if (skip && *skip) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < r; i += nw) {
-        double cx = 0, cy = 0;
-        for (int q = lane; q < r; q += 32) {
-            const double2 m = M[(long)q * r + i], sv = s[q];
-            cx = fmac(m.x, sv.x, cx); cx = fmac(-m.y, sv.y, cx);
-            cy = fmac(m.x, sv.y, cy); cy = fmac(m.y, sv.x, cy);
+// Runtime count -> compile-time CNT in [1, C].
+template <typename VT, int C, bool SCALE>
+__device__ __forceinline__ void proj_group_n(int cnt, const VT* V, long ldv, int g0, int nv, const VT* xin, VT* xout,
+                                             double2* w, double sc, long n, typename acc_of<VT>::type* red,
+                                             const RedScratch& rs) {
+    if (cnt == C) proj_group<VT, C, SCALE>(V, ldv, g0, nv, xin, xout, w, sc, n, red, rs);
+    else if constexpr (C > 1) proj_group_n<VT, C - 1, SCALE>(cnt, V, ldv, g0, nv, xin, xout, w, sc, n, red, rs);
+}
+
+// out[i] = sum_e conj(V_i[e]) w[e] for i < nv; with_norm: out[nv] = ||w||^2 (as the
+// projection of w on itself).  Groups of GV vectors; w is re-read once per group.
+template <typename VT, int GV>
+__global__ void __launch_bounds__(kRedThreads) proj_kernel(const VT* __restrict__ V, long ldv, int nv,
+                                                           const VT* __restrict__ w, long n, int with_norm,
+                                                           double2* out, RedScratch rs, const int* skip, int live) {
+    using A = typename acc_of<VT>::type;
+    constexpr int K = 2 * GV;
+    __shared__ A red[(kRedThreads / 32) * K];
+    const bool off = skip && *skip;
+    if (off && !live) return;
+    const int nvt = nv + (with_norm ? 1 : 0);
+    for (int g0 = 0; g0 < nvt; g0 += GV) {
+        if (off) { zero_partials(g0, K, nvt, rs); continue; }
+        const int cnt = nvt - g0 < GV ? nvt - g0 : GV;
+        proj_group_n<VT, GV, false>(cnt, V, ldv, g0, nv, w, nullptr, nullptr, 1.0, n, red, rs);
+    }
+    reduce_partials(rs, nvt, out);
+}
+
+// Deflation projections of the FP32-inner solves (see k_dots32): complex64 basis and
+// vector, FP32 products and in-block sums; the block that finishes the sums also forms
+// cf = M s in FP32.
+__global__ void __launch_bounds__(kRedThreads, 2) proj32_kernel(const float2* __restrict__ V, long ldv, int nv,
+                                                                float2* x, double2* w, const double* inv, long n,
+                                                                double2* out, const float2* __restrict__ M32,
+                                                                float2* cf, RedScratch rs, const int* skip, int live) {
+    constexpr int GV = 16, K = 2 * GV;     // 16 vectors per pass: 32 running sums, 16 loads in flight
+    __shared__ float red[(kRedThreads / 32) * K];
+    const bool off = skip && *skip;
+    if (off && !live) return;
+    const double sc = inv ? *inv : 1.0;
+    for (int g0 = 0; g0 < nv; g0 += GV) {
+        if (off) { zero_partials(g0, K, nv, rs); continue; }
+        const int cnt = nv - g0 < GV ? nv - g0 : GV;
+        if (inv && g0 == 0) proj_group_n<float2, GV, true>(cnt, V, ldv, g0, nv, x, x, w, sc, n, red, rs);
+        else proj_group_n<float2, GV, false>(cnt, V, ldv, g0, nv, x, nullptr, nullptr, 1.0, n, red, rs);
+    }
+    if (reduce_partials(rs, nv, out) && M32) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            float cx = 0, cy = 0;
+            for (int q = 0; q < nv; q++) {
+                const float2 m = M32[(long)q * nv + i];
+                const double2 sq = __ldcg(&out[q]);
+                const float sx = (float)sq.x, sy = (float)sq.y;
+                cx = fmaf(m.x, sx, cx); cx = fmaf(-m.y, sy, cx);
+                cy = fmaf(m.x, sy, cy); cy = fmaf(m.y, sx, cy);
+            }
+            cf[i] = make_float2(cx, cy);
         }
-        cx = warp_sum_d(cx);
-        cy = warp_sum_d(cy);
-        if (lane == 0) cf[i] = make_float2((float)cx, (float)cy);
     }
 }
 
@@ -146,7 +279,7 @@ __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2
                                                                     const int* skip) {
     if (skip && *skip) return;
     __shared__ float2 cs[kMaxBasis];
-    for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = cf[i];
+    for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = __ldcg(&cf[i]);
     __syncthreads();
     const long stride = (long)gridDim.x * blockDim.x;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -171,17 +304,28 @@ __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2
     }
 }
 
+// 1 / ||w|| from ||w||^2 (1 when the norm is zero or not finite: the vector is left as it is)
+__device__ __forceinline__ double inv_norm(double s2) {
+    const double hn = sqrt(fmax(s2, 0.0));
+    return (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 1.0;
+}
+
 // out = base + sum_i V_i c_i.  Coefficients: c = sign * coef, or c = M s when M != NULL.
+// The sum for a row starts from base and runs through the basis in order in one pair of
+// accumulators (the FP64 pipe, not the FMA latency, bounds the loop).
 template <typename VT, bool NORM>
 __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __restrict__ V, long ldv, int k,
                                                                  const double2* __restrict__ coef, double sign,
                                                                  const double2* __restrict__ M,
                                                                  const double2* __restrict__ s, const double2* base,
                                                                  double2* out, long n, double2* nrm2, Dgks dec,
-                                                                 int has_dec, RedScratch rs, const int* skip) {
+                                                                 int has_dec, RedScratch rs, const int* skip,
+                                                                 int live) {
     using A = typename acc_of<VT>::type;
-    if (skip && *skip) return;
+    const bool off = skip && *skip;
+    if (off && !(NORM && live)) return;
     __shared__ VT cs[kMaxBasis];
+    __shared__ A csn[kMaxBasis];            // -Im(c): every step below is a plain FMA
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         double cx = 0, cy = 0;
         if (M) {
@@ -198,56 +342,38 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
         c.x = (A)cx;
         c.y = (A)cy;
         cs[i] = c;
+        csn[i] = -c.y;
     }
     __syncthreads();
     double nacc = 0;
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        A x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-        int i = 0;
+    const long nn = off ? 0 : n;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nn; idx += stride) {
+        A x0 = 0, y0 = 0;
+        if (base) { const double2 bv = base[idx]; x0 = (A)bv.x; y0 = (A)bv.y; }
 #pragma unroll 4
-        for (; i + 1 < k; i += 2) {
+        for (int i = 0; i < k; i++) {
             const VT a = V[(long)i * ldv + idx], c = cs[i];
-            const VT b = V[(long)(i + 1) * ldv + idx], d = cs[i + 1];
-            x0 = fmac(a.x, c.x, x0); x0 = fmac(-a.y, c.y, x0);
-            y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
-            x1 = fmac(b.x, d.x, x1); x1 = fmac(-b.y, d.y, x1);
-            y1 = fmac(b.x, d.y, y1); y1 = fmac(b.y, d.x, y1);
-        }
-        if (i < k) {
-            const VT a = V[(long)i * ldv + idx], c = cs[i];
-            x0 = fmac(a.x, c.x, x0); x0 = fmac(-a.y, c.y, x0);
+            x0 = fmac(a.x, c.x, x0); x0 = fmac(a.y, csn[i], x0);
             y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
         }
-        double2 o = make_double2((double)x0 + (double)x1, (double)y0 + (double)y1);
-        if (base) { const double2 bv = base[idx]; o.x += bv.x; o.y += bv.y; }
+        const double2 o = make_double2((double)x0, (double)y0);
         out[idx] = o;
         if (NORM) { nacc = fmac(o.x, o.x, nacc); nacc = fmac(o.y, o.y, nacc); }
     }
     if (NORM) {
-        __shared__ double red[kRedThreads / 32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        nacc = warp_sum_d(nacc);
-        if (lane == 0) red[warp] = nacc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0;
-            for (int q = 0; q < kRedThreads / 32; q++) t += red[q];
-            rs.partial[blockIdx.x] = make_double2(t, 0.0);
-        }
-        if (arrive_last(rs.counter)) {
-            __shared__ double2 tot;
-            final_sums(rs.partial, 1, &tot);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                *rs.counter = 0;
-                *nrm2 = tot;
-                if (has_dec) {
-                    const int r = dec.always || tot.x < dec.eta2 * dec.before2->x;
-                    *dec.reorth = r;
-                    *dec.skip2 = (dec.done && *dec.done) || !r;
-                }
+        A acc[2] = {(A)nacc, (A)0};
+        __shared__ A red[(kRedThreads / 32) * 2];
+        block_partials<A, 2, 1>(acc, red, 0, rs);
+        if (reduce_partials(rs, 1, nrm2) && threadIdx.x == 0) {
+            const double tot = __ldcg(&nrm2->x);
+            int r = 0;
+            if (has_dec) {
+                r = dec.always || tot < dec.eta2 * dec.before2->x;
+                *dec.reorth = r;
+                *dec.skip2 = (dec.done && *dec.done) || !r;
             }
+            if (dec.inv && !r) *dec.inv = inv_norm(tot);
         }
     }
 }
@@ -257,24 +383,26 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
 // rotation that annihilates H(j+1, j), update g; residual estimate |g_{j+1}| / ||b||.
 // The column, the stored rotations and g_j are staged in shared memory by the whole
 // block (one global round trip instead of one per rotation), then thread 0 computes.
+// Everything it reads belongs to step j (its own slots of h1, h2, nrm and reorth).
 __global__ void arnoldi_finish_kernel(GmresDev S, int j, int step) {
     __shared__ double2 col[kMaxBasis + 2], csv[kMaxBasis], snv[kMaxBasis];
     if (*S.done) return;
     const int ld = S.m + 1;
     double2* Hgl = S.H + (long)j * ld;
-    const int re = *S.reorth;
+    const double2* h1 = S.h1 + (long)j * (S.m + 3);
+    const double2* h2 = S.h2 + (long)j * (S.m + 3);
+    const int re = S.reorth[j];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        col[i] = re ? make_double2(S.h1[i].x + S.h2[i].x, S.h1[i].y + S.h2[i].y) : S.h1[i];
+        col[i] = re ? make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y) : h1[i];
         if (i < j) { csv[i] = S.cs[i]; snv[i] = S.sn[i]; }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
     double2* Hc = col;
     if (re) *S.nreorth += 1;
-    const double wnorm2 = re ? S.nrm[1].x : S.nrm[0].x;
-    const double before2 = S.h1[j + 1].x;
+    const double wnorm2 = re ? S.nrm[2 * j + 1].x : S.nrm[2 * j].x;
+    const double before2 = h1[j + 1].x;
     const double hn = sqrt(fmax(wnorm2, 0.0));
-    *S.wnorm = hn;
     Hc[j + 1] = make_double2(hn, 0.0);
     for (int i = 0; i < j; i++) {
         const double c = csv[i].x;
@@ -327,16 +455,15 @@ __device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float
 
 __global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32) {
     if (skip && *skip) return;
-    const double s2 = nrm2->x;
-    if (!(s2 > 0.0) || !isfinite(s2)) return;
-    scale_rows(v, n, 1.0 / sqrt(s2), v32);
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) s_inv = inv_norm(nrm2->x);
+    __syncthreads();
+    scale_rows(v, n, s_inv, v32);
 }
 
-__global__ void scale_inv_real_kernel(double2* v, long n, const double* s, const int* skip, float2* v32) {
+__global__ void scale_by_kernel(double2* v, long n, const double* inv, const int* skip, float2* v32) {
     if (skip && *skip) return;
-    const double d = *s;
-    if (!(d != 0.0) || !isfinite(d)) return;
-    scale_rows(v, n, 1.0 / d, v32);
+    scale_rows(v, n, *inv, v32);
 }
 
 __global__ void sub_kernel(const double2* b, const double2* y, double2* r, long n) {
@@ -349,16 +476,27 @@ __global__ void to_c64_kernel(const double2* x, float2* y, long n) {
         y[i] = make_float2((float)x[i].x, (float)x[i].y);
 }
 
+// Back substitution R y = g (R: the rotated k x k Hessenberg), column by column: the
+// reciprocals of the diagonal are formed in parallel first, then y_i = g_i / R_ii and
+// the rest of g is updated by all threads at once, so the serial chain is one complex
+// multiply per column instead of a row of them.
 __global__ void gmres_lsq_kernel(GmresDev S) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double2 rhs[kMaxBasis], rd[kMaxBasis];
     const int k = *S.k, ld = S.m + 1;
-    for (int i = k - 1; i >= 0; i--) {
-        double2 acc = S.g[i];
-        for (int q = i + 1; q < k; q++) acc = csub(acc, cmul(S.H[(long)q * ld + i], S.y[q]));
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        rhs[i] = S.g[i];
         const double2 d = S.H[(long)i * ld + i];
         const double dd = d.x * d.x + d.y * d.y;
-        if (dd == 0.0) { S.y[i] = make_double2(0, 0); *S.flags |= 4; continue; }
-        S.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+        rd[i] = dd == 0.0 ? make_double2(0.0, 0.0) : make_double2(d.x / dd, -d.y / dd);
+        if (dd == 0.0) *S.flags |= 4;
+    }
+    __syncthreads();
+    for (int i = k - 1; i >= 0; i--) {
+        const double2 yi = cmul(rhs[i], rd[i]);
+        __syncthreads();
+        for (int q = threadIdx.x; q < i; q += blockDim.x) rhs[q] = csub(rhs[q], cmul(S.H[(long)i * ld + q], yi));
+        if (threadIdx.x == 0) S.y[i] = yi;
+        __syncthreads();
     }
 }
 
@@ -378,31 +516,35 @@ static inline int grid_for(long n) {
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
+constexpr int kGroupFp64 = 8;        // FP64 projections per group (16 running sums per thread)
+
 die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
-                  const RedScratch& rs, const int* skip, cudaStream_t st) {
+                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live) {
     if (nv + 1 > kMaxBasis || nv < 0) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS, st, dots_kernel<double2><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, with_norm, out, rs, skip));
+    DIE_PROF(PK_DOTS, st, proj_kernel<double2, kGroupFp64><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_dots32(const float2* V, long ldv, int nv, const float2* w, long n, double2* out, const RedScratch& rs,
-                    const int* skip, cudaStream_t st) {
-    if (nv > kMaxBasis || nv < 0) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS32, st, dots_kernel<float2><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, 0, out, rs, skip));
+die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, const double* inv, long n,
+                    double2* out, const float2* M32, float2* cf, const RedScratch& rs, const int* skip,
+                    cudaStream_t st, bool live) {
+    if (nv > kMaxBasis || nv < 1 || (inv && !w)) return DIE_EINVAL;
+    DIE_PROF(PK_DOTS32, st, proj32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, x, w, inv, n, out, M32, cf, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
                         double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs, const int* skip,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool live) {
     if (k > kMaxBasis || k < 0) return DIE_EINVAL;
     const Dgks d = dec ? *dec : Dgks{};
+    const int has_dec = dec && dec->reorth ? 1 : 0;
     if (nrm2) {
         DIE_PROF(PK_UPDATE_NORM, st, basis_axpy_kernel<double2, true><<<kRedBlocks, kRedThreads, 0, st>>>(
-                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nrm2, d, dec ? 1 : 0, rs, skip));
+                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0));
     } else {
         DIE_PROF(PK_LINCOMB, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
-                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nullptr, d, 0, rs, skip));
+                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nullptr, d, 0, rs, skip, 0));
     }
     DIE_LAUNCH_CHECK();
     return DIE_OK;
@@ -411,34 +553,37 @@ die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, co
                          double2* z, long n, const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
     DIE_PROF(PK_DEFL_UPDATE, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
-                 V, ldv, r, nullptr, 1.0, M, s, x, z, n, nullptr, Dgks{}, 0, RedScratch{}, skip));
+                 V, ldv, r, nullptr, 1.0, M, s, x, z, n, nullptr, Dgks{}, 0, RedScratch{}, skip, 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, float2* cf,
-                           const float2* x, float2* z, long n, const int* skip, cudaStream_t st) {
+die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
+                           const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
-    DIE_PROF(PK_SMALL, st, defl_coef_kernel<<<1, 256, 0, st>>>(M, s, r, cf, skip));
     DIE_PROF(PK_DEFL_UPDATE, st, defl_update32_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, cf, x, z, n, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
-                    int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st) {
+                    int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st,
+                    double* inv) {
     Dgks dec;
     dec.before2 = h1 + nv;
     dec.reorth = reorth;
     dec.skip2 = skip2;
     dec.done = done;
+    dec.inv = inv;
     dec.always = eta2 >= 1.0 ? 1 : 0;
     dec.eta2 = eta2;
-    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st));
-    DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st));
+    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true));
+    DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true));
+    Dgks last;                       // second pass: no decision, only the scale factor
+    last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;
     die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st);
     g_prof_override = PK_UPDATE_REORTH;
-    if (s == DIE_OK) s = k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, nullptr, rs, skip2, st);
+    if (s == DIE_OK) s = k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st);
     g_prof_override = -1;
     return s;
 }
@@ -448,8 +593,8 @@ die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* 
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_scale_inv_real(double2* v, long n, const double* s, const int* skip, cudaStream_t st, float2* v32) {
-    DIE_PROF(PK_SCALE, st, scale_inv_real_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, s, skip, v32));
+die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st, float2* v32) {
+    DIE_PROF(PK_SCALE, st, scale_by_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, inv, skip, v32));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -464,12 +609,12 @@ die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st) {
     return DIE_OK;
 }
 die_status k_arnoldi_finish(GmresDev S, int j, int step, cudaStream_t st) {
-    DIE_PROF(PK_SMALL, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j, step));
+    DIE_PROF(PK_GIVENS, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j, step));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 die_status k_gmres_lsq(GmresDev S, cudaStream_t st) {
-    DIE_PROF(PK_SMALL, st, gmres_lsq_kernel<<<1, 32, 0, st>>>(S));
+    DIE_PROF(PK_SMALL, st, gmres_lsq_kernel<<<1, 64, 0, st>>>(S));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -126,6 +126,7 @@ static void free_defl(defl_s* d) {
     if (d->M) cudaFree(d->M);
     if (d->V32) cudaFree(d->V32);
     if (d->c32) cudaFree(d->c32);
+    if (d->M32) cudaFree(d->M32);
     if (d->s) cudaFree(d->s);
     free_red_scratch(&d->rs);
     delete d;
@@ -286,6 +287,8 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     DIE_TRY(k_to_c64(d->V, d->V32, (long)r * n, st));
     inverse_minus_identity_kernel<<<1, 32, 0, st>>>(d->M, r, w.ist + 4, w.ist);
     DIE_LAUNCH_CHECK();
+    DIE_TRY(dalloc((void**)&d->M32, (size_t)r * r * sizeof(float2)));
+    DIE_TRY(k_to_c64(d->M, d->M32, (long)r * r, st));
     int rc = 0;
     DIE_CUDA_TRY(cudaMemcpyAsync(&rc, w.ist, sizeof(int), cudaMemcpyDeviceToHost, st));
     DIE_CUDA_TRY(cudaStreamSynchronize(st));

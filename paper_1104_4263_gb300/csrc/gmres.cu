@@ -1,18 +1,20 @@
 // Restarted GMRES(m) (Saad & Schultz) on Atilde = A or A_R A (Section 5), with the
 // deflating right preconditioner of Eq. (4.12): Atilde P^-1 v = btilde, x = P^-1 v.
 //
-// One cycle runs entirely on the device without host round trips: each Arnoldi
-// vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion (a
-// second pass only when the first one cancelled more than half of ||w||^2; the
-// device decides, and the second-pass kernels return at once when it is not
-// needed), the new Hessenberg column is rotated by Givens rotations on the device,
-// and when the residual estimate reaches tol a device flag makes the remaining
-// kernels of the cycle return at once.  The host reads one flag set per cycle.
-// Between cycles the residual btilde - Atilde x is recomputed in FP64 (in the
-// FP32-inner form this is the iterative-refinement step).
+// One cycle runs entirely on the device without host round trips.  Each Arnoldi
+// vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion: a second
+// pass runs only when the first one left less than eta of ||w|| (eta = 0.01 unless the
+// caller sets it); the device decides, and the second-pass kernels return at once when
+// it is not needed.  The new Hessenberg column is rotated by Givens rotations on the
+// device, on a side stream one step behind, since the next Arnoldi step does not need
+// the rotations; the normalisation of the new vector uses 1 / ||w|| from the last
+// Gram-Schmidt kernel.  When the residual estimate reaches tol the Givens step sets a
+// device flag that makes the kernels of the remaining steps skip their work.  The host
+// reads one flag set per cycle.  Between cycles the residual btilde - Atilde x is
+// recomputed in FP64 (in the FP32-inner form this is the iterative-refinement step).
 //
 // FP32-inner form: the products with Atilde inside a cycle run in complex64 and the
-// deflation P^-1 uses a complex64 copy of V with FP32 sums (P^-1 is one fixed
+// deflation P^-1 uses a complex64 copy of V and M with FP32 sums (P^-1 is one fixed
 // preconditioner for the whole solve, so its rounding only changes the
 // preconditioner, and the FP64 restart residual corrects the iterate).  Arnoldi,
 // least squares and the restart residual are FP64 in both forms.
@@ -26,15 +28,17 @@
 namespace die {
 
 die_status alloc_red_scratch(RedScratch* rs) {
-    if (cudaMalloc((void**)&rs->partial, (size_t)kMaxBasis * kRedBlocks * sizeof(double2)) != cudaSuccess) {
+    if (cudaMalloc((void**)&rs->partial, (size_t)kMaxBasis * (kRedBlocks + kRedGroups) * sizeof(double2)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return DIE_ENOMEM;
     }
-    if (cudaMalloc((void**)&rs->counter, sizeof(unsigned)) != cudaSuccess) {
+    rs->partial2 = rs->partial + (size_t)kMaxBasis * kRedBlocks;
+    if (cudaMalloc((void**)&rs->counter, kRedCounters * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return DIE_ENOMEM;
     }
-    DIE_CUDA_TRY(cudaMemset(rs->counter, 0, sizeof(unsigned)));
+    DIE_CUDA_TRY(cudaMemset(rs->counter, 0, kRedCounters * sizeof(unsigned)));
     return DIE_OK;
 }
 
@@ -42,6 +46,7 @@ void free_red_scratch(RedScratch* rs) {
     if (rs->partial) cudaFree(rs->partial);
     if (rs->counter) cudaFree(rs->counter);
     rs->partial = nullptr;
+    rs->partial2 = nullptr;
     rs->counter = nullptr;
 }
 
@@ -50,20 +55,23 @@ SolverCache* solver_cache(dieop_s* op) { return reinterpret_cast<SolverCache*>(o
 void free_solver_cache(dieop_s* op) {
     SolverCache* c = solver_cache(op);
     if (!c) return;
-    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->wnorm, c->one};
+    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->one};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_red_scratch(&c->rs);
     if (c->host) cudaFreeHost(c->host);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : c->join)
+    for (cudaEvent_t e : {c->join[0], c->join[1], c->fork, c->back})
         if (e) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
     op->solver = nullptr;
 }
 
-static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 4 * (m + 3) + 16; }
+// H, cs, sn, g, h1 and h2 (m slots of m+3), y, nrm (2 per step), scale factors, scalars
+static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 2 * (m + 3) + 2 * (size_t)m * (m + 3) + 3 * m + 16; }
+static int ints_count(int m) { return 8 + m; }
 
 die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     SolverCache* c = solver_cache(op);
@@ -84,8 +92,8 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
               al((void**)&c->tmp, n * sizeof(double2)) && al((void**)&c->z, n * sizeof(double2)) &&
               al((void**)&c->v32, n * sizeof(float2)) && al((void**)&c->z32, n * sizeof(float2)) &&
               al((void**)&c->small, small_count(m) * sizeof(double2)) &&
-              al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) && al((void**)&c->ints, 16 * sizeof(int)) &&
-              al((void**)&c->wnorm, 8 * sizeof(double)) && al((void**)&c->one, sizeof(double2));
+              al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) &&
+              al((void**)&c->ints, ints_count(m) * sizeof(int)) && al((void**)&c->one, sizeof(double2));
     if (!ok) {
         cudaGetLastError();
         free_solver_cache(op);
@@ -100,21 +108,25 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     const double2 one = make_double2(1.0, 0.0);
     DIE_CUDA_TRY(cudaMemcpy(c->one, &one, sizeof one, cudaMemcpyHostToDevice));
     DIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    DIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     for (auto& e : c->join) DIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->back, cudaEventDisableTiming));
     c->ev.resize(4 * (size_t)(m + 1));
     for (auto& e : c->ev) DIE_CUDA_TRY(cudaEventCreate(&e));
     return DIE_OK;
 }
 
-die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st) {
-    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, 0, d->s, d->rs, skip, st));
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live) {
+    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, 0, d->s, d->rs, skip, st, live));
     DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
-die_status defl_apply32(defl_s* d, const float2* x, float2* z, const int* skip, cudaStream_t st) {
-    DIE_TRY(k_dots32(d->V32, d->n, d->r, x, d->n, d->s, d->rs, skip, st));
-    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->M, d->s, d->c32, x, z, d->n, skip, st));
+die_status defl_apply32(defl_s* d, float2* x, double2* w, const double* inv, float2* z, const int* skip,
+                        cudaStream_t st, bool live) {
+    DIE_TRY(k_dots32(d->V32, d->n, d->r, x, w, inv, d->n, d->s, d->M32, d->c32, d->rs, skip, st, live));
+    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->c32, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
@@ -213,14 +225,18 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     // The solve runs on the library's own stream, ordered after the caller's stream at
     // entry and before it at every exit (a stream of its own can carry the L2
     // access-policy window below, which the legacy default stream cannot).
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream, side = c->side;
     DIE_CUDA_TRY(cudaEventRecord(c->join[0], ust));
     DIE_CUDA_TRY(cudaStreamWaitEvent(st, c->join[0], 0));
+    // at every exit: the side stream joins the solve's stream, which joins the caller's
     struct Join {
-        cudaStream_t from, to;
-        cudaEvent_t ev;
-        ~Join() { if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0); }
-    } join{st, ust, c->join[1]};
+        cudaStream_t side, from, to;
+        cudaEvent_t back, ev;
+        ~Join() {
+            if (cudaEventRecord(back, side) == cudaSuccess) cudaStreamWaitEvent(from, back, 0);
+            if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+        }
+    } join{side, st, ust, c->back, c->join[1]};
     const double2* b = (const double2*)b_;
     double2* x = (double2*)x_;
 
@@ -231,24 +247,24 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     S.cs = sm; sm += m;
     S.sn = sm; sm += m;
     S.g = sm; sm += m + 3;
-    S.h1 = sm; sm += m + 3;
-    S.h2 = sm; sm += m + 3;
+    S.h1 = sm; sm += (size_t)m * (m + 3);
+    S.h2 = sm; sm += (size_t)m * (m + 3);
     S.y = sm; sm += m + 3;
-    S.nrm = sm; sm += 4;
+    S.nrm = sm; sm += 2 * m;
+    S.inv = reinterpret_cast<double*>(sm); sm += m;
     double2* scal = sm;            // scalars: [0] residual norm^2
     S.hist = c->hist;
     S.done = c->ints;
     S.k = c->ints + 1;
     S.flags = c->ints + 2;
-    S.reorth = c->ints + 3;
-    S.skip2 = c->ints + 4;
-    S.nreorth = c->ints + 5;
-    S.wnorm = c->wnorm;
+    S.skip2 = c->ints + 3;
+    S.nreorth = c->ints + 4;
+    S.reorth = c->ints + 8;
     S.m = m;
     S.jmax = m;
     S.hist_cap = c->hist_cap;
     S.tol = o->tol;
-    DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, 16 * sizeof(int), st));
+    DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, ints_count(m) * sizeof(int), st));
 
     // right-hand side of the solved system
     const double2* bt = b;
@@ -271,7 +287,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     const long ldv = n;
     double2* V = c->V;
     // FP32-inner with deflation: P^-1 v_j and the product input stay complex64; the
-    // normalising kernel keeps a complex64 copy of the current Arnoldi vector.
+    // deflation projections of step j normalise v_j (scaled by 1 / ||w|| of step j-1)
+    // and keep its complex64 copy.
     const bool defl32 = defl && mixed;
     float2* v32 = defl32 ? c->v32 : nullptr;
     // the complex64 deflation basis is read twice per Arnoldi step: keep it in L2
@@ -299,30 +316,40 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         DIE_TRY(k_gmres_init(S, scal, st));
         const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
         S.jmax = jmax;
+        // Step j: v_j = w_{j-1} / ||w_{j-1}|| (j > 0), w = Atilde P^-1 v_j, Gram-Schmidt
+        // against v_0..v_j on this stream; the Givens step of j then runs on the side
+        // stream while step j+1 starts.  The done flag it sets is read by the kernels
+        // of later steps as a live skip flag.
         for (int j = 0; j < jmax; j++) {
-            const double2* vj = V + (long)j * ldv;
+            double2* vj = V + (long)j * ldv;
             double2* w = V + (long)(j + 1) * ldv;
+            const double* inv_prev = j > 0 ? S.inv + (j - 1) : nullptr;
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j], st));
             if (defl32) {
-                DIE_TRY(defl_apply32(defl, c->v32, c->z32, S.done, st));
+                DIE_TRY(defl_apply32(defl, c->v32, j > 0 ? vj : nullptr, inv_prev, c->z32, S.done, st, true));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
                 DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
                             : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
             } else {
+                if (inv_prev) DIE_TRY(k_scale_by(vj, n, inv_prev, S.done, st));
                 const double2* src = vj;
                 if (defl) {
-                    DIE_TRY(defl_apply(defl, vj, c->z, S.done, st));
+                    DIE_TRY(defl_apply(defl, vj, c->z, S.done, st, true));
                     src = c->z;
                 }
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
                 DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st));
             }
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
-            DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1, S.h2, S.nrm, S.reorth, S.skip2, S.done, eta2, c->rs, st));
-            DIE_TRY(k_arnoldi_finish(S, j, iters + j, st));
-            DIE_TRY(k_scale_inv_real(w, n, S.wnorm, S.done, st, v32));
+            DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1 + (long)j * (m + 3), S.h2 + (long)j * (m + 3), S.nrm + 2 * j,
+                             S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
+            DIE_CUDA_TRY(cudaEventRecord(c->fork, st));
+            DIE_CUDA_TRY(cudaStreamWaitEvent(side, c->fork, 0));
+            DIE_TRY(k_arnoldi_finish(S, j, iters + j, side));
         }
+        DIE_CUDA_TRY(cudaEventRecord(c->back, side));
+        DIE_CUDA_TRY(cudaStreamWaitEvent(st, c->back, 0));
         int hk[8];
         DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));

@@ -13,86 +13,111 @@ namespace die {
 
 constexpr int kRedBlocks = 304;      // 2 blocks per SM on a 152-SM GB300; fixed => deterministic sums
 constexpr int kRedThreads = 256;
+constexpr int kRedGroup = 16;        // blocks per first-level group of the final sums
+constexpr int kRedGroups = kRedBlocks / kRedGroup;
 constexpr int kMaxBasis = 320;       // largest basis a single call handles
+static_assert(kRedBlocks % kRedGroup == 0, "reduction groups must tile the grid");
 
-// Reduction scratch: per-block partial sums, [vector][block], and the arrival counter
-// of the last-block reduction (left at 0 by every kernel that uses it).
+// Reduction scratch.  Each block writes one partial per vector ([vector][block]); the
+// last block of each group of kRedGroup consecutive blocks to arrive sums the group's
+// partials in block order ([vector][group]); the last group to finish sums those in
+// group order.  The arrival counters (one per group, then the top one) are left at 0
+// by every kernel that uses them.
 struct RedScratch {
     double2* partial = nullptr;      // kMaxBasis * kRedBlocks
-    unsigned* counter = nullptr;
+    double2* partial2 = nullptr;     // kMaxBasis * kRedGroups
+    unsigned* counter = nullptr;     // kRedCounters
 };
+constexpr int kRedCounters = 1 + kRedGroups;
 
 // DGKS decision taken by the last block of a norm-computing update: reorth = always ||
 // ||w'||^2 < eta^2 ||w||^2; skip2 = done || !reorth (makes the second pass return at once).
+// When inv != NULL the block that holds the final norm of w also stores 1 / ||w|| there
+// (1 when the norm is zero or not finite), for the normalisation of the next basis vector.
 struct Dgks {
     const double2* before2 = nullptr;  // ||w||^2 before the first pass (real part)
     int* reorth = nullptr;
     int* skip2 = nullptr;
     const int* done = nullptr;         // may be NULL
+    double* inv = nullptr;             // may be NULL
     int always = 0;
     double eta2 = 0.5;
 };
 
-// State of one GMRES cycle on the device (all FP64).
+// State of one GMRES cycle on the device (all FP64).  The per-step arrays (projections,
+// norms, DGKS flag, scale factor) have one slot per Arnoldi step, so that the Givens
+// step of step j, which runs on a side stream, reads values that step j+1 does not
+// overwrite.
 struct GmresDev {
     double2* H;        // (m+1) x m, column-major, ld = m+1: Hessenberg, rotated in place to R
     double2* cs;       // m rotation cosines (real part used)
     double2* sn;       // m rotation sines
     double2* g;        // m+1: rotated beta e1
-    double2* h1;       // m+3: first projections (+ ||w||^2 at index j+1)
-    double2* h2;       // m+3: second projections (re-orthogonalisation)
+    double2* h1;       // m x (m+3): step j's first projections at h1 + j (m+3) (+ ||w||^2 at index j+1)
+    double2* h2;       // m x (m+3): second projections (re-orthogonalisation)
     double2* y;        // m: least-squares solution
-    double2* nrm;      // [0]: ||w||^2 after pass 1, [1]: after pass 2
+    double2* nrm;      // 2 m: step j: [2j] ||w||^2 after pass 1, [2j+1] after pass 2
+    double* inv;       // m: step j: 1 / ||w|| after orthogonalisation (scales v_{j+1})
     double* hist;      // per-step residual estimates (relative), indexed by global step
     int* done;         // 1 when the cycle must stop (converged / breakdown / NaN)
     int* k;            // steps completed in the current cycle
     int* flags;        // bit 0: NaN/Inf met, bit 1: Arnoldi breakdown, bit 2: singular R
-    int* reorth;       // 1 if the second Gram-Schmidt pass ran this step
-    int* skip2;        // done || !reorth
+    int* reorth;       // m: 1 if the second Gram-Schmidt pass ran at step j
+    int* skip2;        // done || !reorth of the current step
     int* nreorth;      // second passes run (counter over the solve)
-    double* wnorm;     // ||w|| after orthogonalisation (= H(j+1, j))
     double bnorm, tol;
     int m, jmax, hist_cap;
 };
 
+// Skip flags: the kernels return at once when *skip != 0.  A "live" flag is one that
+// another stream may set while the kernel runs (the GMRES done flag, set by the Givens
+// step on its side stream): the reduction kernels then skip only their own work and
+// still take part in the final sums, so that the arrival counters stay consistent.
+//
 // out[i] = V_i^* w for i < nv; with_norm: out[nv] = ||w||^2 (real part).
 die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
-                  const RedScratch& rs, const int* skip, cudaStream_t st);
-// The same with a complex64 basis and vector, FP32 accumulation within each lane.
-die_status k_dots32(const float2* V, long ldv, int nv, const float2* w, long n, double2* out,
-                    const RedScratch& rs, const int* skip, cudaStream_t st);
+                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live = false);
+// Deflation projections of the FP32-inner solves: s = V^* x with a complex64 basis and
+// vector (FP32 products and in-block sums, FP64 across blocks), then cf = M s rounded to
+// complex64 (M32: the r x r matrix M in complex64, column-major).  With inv != NULL, x
+// is first formed from the FP64 vector w: w *= *inv (written back) and x = w in complex64.
+die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, const double* inv, long n,
+                    double2* out, const float2* M32, float2* cf, const RedScratch& rs, const int* skip,
+                    cudaStream_t st, bool live = false);
 // out = base + sign * sum_i V_i c_i (base may be NULL = 0, out may equal base), c = coef.
 // nrm2 != NULL: ||out||^2 into nrm2[0] (device), and the DGKS decision if dec != NULL.
 die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
                         double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs,
-                        const int* skip, cudaStream_t st);
+                        const int* skip, cudaStream_t st, bool live = false);
 // z = x + V (M s); M r x r column-major; s the projections V^* x.  z may equal x.
 die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
                          double2* z, long n, const int* skip, cudaStream_t st);
-// All-complex64 deflation update (FP32-inner solves): cf = M s (rounded, r entries of
-// device scratch), then z = x + V cf.
-die_status k_defl_update32(const float2* V, long ldv, int r, const double2* M, const double2* s, float2* cf,
-                           const float2* x, float2* z, long n, const int* skip, cudaStream_t st);
+// All-complex64 deflation update (FP32-inner solves): z = x + V cf, cf from k_dots32.
+die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
+                           const int* skip, cudaStream_t st);
 
-// Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion:
+// Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion (done is a
+// live flag, see above):
 // h1 = V^* w (||w||^2 in h1[nv]); w -= V h1 (||w||^2 -> nrm[0]); if ||w||^2 < eta2
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
+// inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2,
                     double2* nrm, int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs,
-                    cudaStream_t st);
+                    cudaStream_t st, double* inv = nullptr);
 
-// v *= 1 / sqrt(re(*nrm2)) if positive; v *= 1 / *s if non-zero.  v32 != NULL also
-// receives the scaled vector rounded to complex64.
+// v *= 1 / sqrt(re(*nrm2)) if positive; v *= *inv.  v32 != NULL also receives the
+// scaled vector rounded to complex64.
 die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st,
                             float2* v32 = nullptr);
-die_status k_scale_inv_real(double2* v, long n, const double* s, const int* skip, cudaStream_t st,
-                            float2* v32 = nullptr);
+die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st,
+                      float2* v32 = nullptr);
 // r = b - y
 die_status k_sub(const double2* b, const double2* y, double2* r, long n, cudaStream_t st);
 // complex128 -> complex64 copy
 die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st);
 
 // GMRES step j after Gram-Schmidt: H(:, j) = h1 (+ h2), H(j+1, j) = ||w||, Givens.
+// Reads only step j's slots, so it may run on a side stream behind the next step.
 die_status k_arnoldi_finish(GmresDev S, int j, int step, cudaStream_t st);
 // Solve the k x k upper-triangular R y = g of the current cycle (k read from S.k).
 die_status k_gmres_lsq(GmresDev S, cudaStream_t st);

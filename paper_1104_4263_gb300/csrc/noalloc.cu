@@ -1,9 +1,9 @@
 // deflation_apply_noalloc: z = P^-1 x = x + V (M (V^* x)) without any device
 // allocation.  It runs the same two kernels as deflation_apply (batched projections
-// with a deterministic last-block reduction, then the rank-r update), but their
-// scratch -- the per-block partial sums, the r projections and the arrival counter of
-// the reduction -- lives in the file-scope array below instead of buffers allocated
-// by deflation_build.
+// with a deterministic two-level reduction, then the rank-r update), but their
+// scratch -- the per-block and per-group partial sums, the r projections and the
+// arrival counters of the reduction -- lives in the file-scope array below instead of
+// buffers allocated by deflation_build.
 #include <mutex>
 
 #include "solver.cuh"
@@ -13,11 +13,13 @@ namespace die {
 constexpr int kNoAllocMaxR = 128;                // largest deflation rank accepted
 constexpr int kNoAllocMaxDevices = 64;
 constexpr long kNoAllocPartials = (long)kNoAllocMaxR * kRedBlocks;
-// partials | projections s | counter (one double2 slot)
-constexpr long kNoAllocSlots = kNoAllocPartials + kNoAllocMaxR + 1;
+constexpr long kNoAllocPartials2 = (long)kNoAllocMaxR * kRedGroups;
+constexpr long kNoAllocCounterSlots = (kRedCounters * sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
+// block partials | group partials | projections s | counters
+constexpr long kNoAllocSlots = kNoAllocPartials + kNoAllocPartials2 + kNoAllocMaxR + kNoAllocCounterSlots;
 
-// 128 * 304 * 16 + 129 * 16 bytes (about 625 KB), held by every GPU that loads the
-// library until the process exits.
+// (128 * 304 + 128 * 19 + 128 + 5) * 16 bytes (about 650 KB), held by every GPU that
+// loads the library until the process exits.
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
 
 static std::mutex g_noalloc_mu;
@@ -54,10 +56,11 @@ extern "C" die_status deflation_apply_noalloc(defl_t d, const void* x, void* z, 
     cudaStream_t st = (cudaStream_t)stream;
     RedScratch rs;
     rs.partial = base;
-    rs.counter = reinterpret_cast<unsigned*>(base + kNoAllocPartials + kNoAllocMaxR);
-    double2* s = base + kNoAllocPartials;
-    // the reduction's arrival counter must start at zero
-    DIE_CUDA_TRY(cudaMemsetAsync(rs.counter, 0, sizeof(unsigned), st));
+    rs.partial2 = base + kNoAllocPartials;
+    double2* s = base + kNoAllocPartials + kNoAllocPartials2;
+    rs.counter = reinterpret_cast<unsigned*>(s + kNoAllocMaxR);
+    // the reduction's arrival counters must start at zero
+    DIE_CUDA_TRY(cudaMemsetAsync(rs.counter, 0, kRedCounters * sizeof(unsigned), st));
     DIE_TRY(k_dots(d->V, d->n, d->r, (const double2*)x, d->n, 0, s, rs, nullptr, st));
     DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, s, (const double2*)x, (double2*)z, d->n, nullptr, st));
     return DIE_OK;

@@ -35,7 +35,7 @@ cudaEvent_t next_event() {
 }
 const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_fwd", "dots", "dots32",
                                 "cgs_update_norm", "dots_reorth", "update_reorth", "scale",
-                                "defl_update", "lincomb", "small_dense", "other"};
+                                "defl_update", "lincomb", "small_dense", "givens", "other"};
 }  // namespace
 
 void prof_mark(int id, cudaStream_t st, int stop) {

@@ -21,6 +21,7 @@ enum ProfKernel {
     PK_DEFL_UPDATE,       // deflation z = x + V (M s)
     PK_LINCOMB,           // x += V y
     PK_SMALL,             // single-thread small dense work
+    PK_GIVENS,            // GMRES Givens step (side stream)
     PK_OTHER,
     PK_COUNT
 };

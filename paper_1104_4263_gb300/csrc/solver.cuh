@@ -19,16 +19,17 @@ struct SolverCache {
     double2* z = nullptr;
     float2* v32 = nullptr;      // complex64 copy of the current Arnoldi vector (FP32-inner + deflation)
     float2* z32 = nullptr;      // complex64 P^-1 v of the FP32-inner form
-    double2* small = nullptr;   // H, cs, sn, g, h1, h2, y, scalars
+    double2* small = nullptr;   // H, cs, sn, g, per-step h1, h2, nrm, scale factors, y, scalars
     double* hist = nullptr;
-    int* ints = nullptr;        // done, k, flags
-    double* wnorm = nullptr;
+    int* ints = nullptr;        // done, k, flags, skip2, nreorth, then the per-step DGKS flags
     double2* one = nullptr;     // device constant 1 + 0i
     RedScratch rs;
     double* host = nullptr;     // pinned readback area
     std::vector<cudaEvent_t> ev;
     cudaStream_t stream = nullptr;  // internal stream of the solves (joined to the caller's)
+    cudaStream_t side = nullptr;    // Givens steps, one step behind the Arnoldi steps
     cudaEvent_t join[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, back = nullptr;   // stream -> side, side -> stream
 };
 
 void free_solver_cache(dieop_s* op);
@@ -47,6 +48,7 @@ struct defl_s {
     int regularized = 0;
     double2* V = nullptr;       // r * n, vector i at V + i * n
     float2* V32 = nullptr;      // complex64 copy of V (FP32-inner solves)
+    float2* M32 = nullptr;      // complex64 copy of M (FP32-inner solves)
     float2* c32 = nullptr;      // r coefficients M (V^* x), complex64 (scratch)
     double2* M = nullptr;       // r * r, column-major
     double2* s = nullptr;       // r projections (scratch)
@@ -55,8 +57,10 @@ struct defl_s {
 };
 
 namespace die {
-// z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip` as for the Krylov kernels.
-die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st);
-// The same entirely in complex64 (copy of V, FP32 sums), for the FP32-inner solves.
-die_status defl_apply32(defl_s* d, const float2* x, float2* z, const int* skip, cudaStream_t st);
+// z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip`, `live` as for the Krylov kernels.
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live = false);
+// The same entirely in complex64 (copy of V, FP32 sums), for the FP32-inner solves.  With
+// inv != NULL the input is first formed from the FP64 vector w: w *= *inv, x = complex64(w).
+die_status defl_apply32(defl_s* d, float2* x, double2* w, const double* inv, float2* z, const int* skip,
+                        cudaStream_t st, bool live = false);
 }  // namespace die
