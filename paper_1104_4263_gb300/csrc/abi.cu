@@ -20,6 +20,14 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
     if (getenv("DIE_LOG")) fprintf(stderr, "libdie: %s\n", g_last_error);
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("DIE_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st);
 die_status compute_contrasts(dieop_s* op, const double2* eps_dev, cudaStream_t st);
 

@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kRedThreads) proj_kernel(const VT* __restrict_
     using A = typename acc_of<VT>::type;
     constexpr int K = 2 * GV;
     __shared__ A red[(kRedThreads / 32) * K];
+    pdl_wait();
     const bool off = skip && *skip;
     if (off && !live) return;
     const int nvt = nv + (with_norm ? 1 : 0);
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) proj32_kernel(const float2* __
                                                                 float2* cf, RedScratch rs, const int* skip, int live) {
     constexpr int GV = 16, K = 2 * GV;     // 16 vectors per pass: 32 running sums, 16 loads in flight
     __shared__ float red[(kRedThreads / 32) * K];
+    pdl_wait();
     const bool off = skip && *skip;
     if (off && !live) return;
     const double sc = inv ? *inv : 1.0;
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2
                                                                     const float2* __restrict__ cf,
                                                                     const float2* x, float2* z, long n,
                                                                     const int* skip) {
+    pdl_wait();
     if (skip && *skip) return;
     __shared__ float2 cs[kMaxBasis];
     for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = __ldcg(&cf[i]);
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
                                                                  int has_dec, RedScratch rs, const int* skip,
                                                                  int live) {
     using A = typename acc_of<VT>::type;
+    pdl_wait();
     const bool off = skip && *skip;
     if (off && !(NORM && live)) return;
     __shared__ VT cs[kMaxBasis];
@@ -454,6 +458,7 @@ __device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float
 }
 
 __global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32) {
+    pdl_wait();
     if (skip && *skip) return;
     __shared__ double s_inv;
     if (threadIdx.x == 0) s_inv = inv_norm(nrm2->x);
@@ -462,6 +467,7 @@ __global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, c
 }
 
 __global__ void scale_by_kernel(double2* v, long n, const double* inv, const int* skip, float2* v32) {
+    pdl_wait();
     if (skip && *skip) return;
     scale_rows(v, n, *inv, v32);
 }
@@ -521,7 +527,7 @@ constexpr int kGroupFp64 = 8;        // FP64 projections per group (16 running s
 die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
                   const RedScratch& rs, const int* skip, cudaStream_t st, bool live) {
     if (nv + 1 > kMaxBasis || nv < 0) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS, st, proj_kernel<double2, kGroupFp64><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
+    DIE_PROF(PK_DOTS, st, launch_pdl(proj_kernel<double2, kGroupFp64>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -529,7 +535,7 @@ die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, co
                     double2* out, const float2* M32, float2* cf, const RedScratch& rs, const int* skip,
                     cudaStream_t st, bool live) {
     if (nv > kMaxBasis || nv < 1 || (inv && !w)) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS32, st, proj32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, nv, x, w, inv, n, out, M32, cf, rs, skip, live ? 1 : 0));
+    DIE_PROF(PK_DOTS32, st, launch_pdl(proj32_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, x, w, inv, n, out, M32, cf, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -540,11 +546,11 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
     const Dgks d = dec ? *dec : Dgks{};
     const int has_dec = dec && dec->reorth ? 1 : 0;
     if (nrm2) {
-        DIE_PROF(PK_UPDATE_NORM, st, basis_axpy_kernel<double2, true><<<kRedBlocks, kRedThreads, 0, st>>>(
-                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0));
+        DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(basis_axpy_kernel<double2, true>, dim3(kRedBlocks), dim3(kRedThreads), 0, st,
+                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0));
     } else {
-        DIE_PROF(PK_LINCOMB, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
-                     V, ldv, k, coef, sign, nullptr, nullptr, base, out, n, nullptr, d, 0, rs, skip, 0));
+        DIE_PROF(PK_LINCOMB, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
+                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, (double2*)nullptr, d, 0, rs, skip, 0));
     }
     DIE_LAUNCH_CHECK();
     return DIE_OK;
@@ -552,15 +558,15 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
 die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
                          double2* z, long n, const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, basis_axpy_kernel<double2, false><<<grid_for(n), kRedThreads, 0, st>>>(
-                 V, ldv, r, nullptr, 1.0, M, s, x, z, n, nullptr, Dgks{}, 0, RedScratch{}, skip, 0));
+    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
+                 V, ldv, r, (const double2*)nullptr, 1.0, M, s, x, z, n, (double2*)nullptr, Dgks{}, 0, RedScratch{}, skip, 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
                            const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, defl_update32_kernel<<<grid_for(n), kRedThreads, 0, st>>>(V, ldv, r, cf, x, z, n, skip));
+    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(defl_update32_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, V, ldv, r, cf, x, z, n, skip));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -589,12 +595,12 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
 }
 
 die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32) {
-    DIE_PROF(PK_SCALE, st, scale_inv_sqrt_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, nrm2, skip, v32));
+    DIE_PROF(PK_SCALE, st, launch_pdl(scale_inv_sqrt_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, nrm2, skip, v32));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st, float2* v32) {
-    DIE_PROF(PK_SCALE, st, scale_by_kernel<<<grid_for(n), kRedThreads, 0, st>>>(v, n, inv, skip, v32));
+    DIE_PROF(PK_SCALE, st, launch_pdl(scale_by_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, inv, skip, v32));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

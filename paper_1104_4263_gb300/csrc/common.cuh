@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/die.h"
 
 namespace die {
@@ -52,6 +54,35 @@ template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return ma
 template <> __device__ __forceinline__ double2 cvt<double2>(float2 a) { return make_double2(a.x, a.y); }
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+// ------------------------------------------------ programmatic dependent launch
+// The kernels of an Arnoldi step (and of the products) are launched with programmatic
+// stream serialisation: the launch of a kernel's grid overlaps the exit of the previous
+// kernel's last blocks, and the kernel waits in pdl_wait for that kernel's completion
+// and memory before reading anything an earlier kernel wrote (skip flags included);
+// work that needs none of it (staging operator constants) may come before the wait.
+// The trigger is the implicit one at block exit: an explicit early trigger made the
+// successor's blocks resident while the predecessor still ran and slowed both.  On a
+// normal launch pdl_wait is a no-op.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+bool pdl_enabled();   // false when the environment sets DIE_PDL=0
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace die
 

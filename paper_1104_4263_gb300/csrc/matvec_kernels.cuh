@@ -25,6 +25,7 @@
 // compile time so that radices, strides and indices are constants.
 #pragma once
 
+#include "fft_fast.cuh"
 #include "op.cuh"
 #include "prof.cuh"
 
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(512) k1_rows_fwd(OpDev<T> op, const IO* __rest
                                                    const C_t<T>* __restrict__ chi, C_t<T>* __restrict__ W,
                                                    const int* __restrict__ skip) {
     using C = C_t<T>;
+    pdl_wait();
     if (skip && *skip) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false);
     const FftPlan pl = LS ? kf : op.f1;
@@ -98,6 +100,7 @@ template <typename T, int EPT, int LS>
 __global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__ W, int stage_g,
                                                const int* __restrict__ skip) {
     using C = C_t<T>;
+    pdl_wait();
     if (skip && *skip) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const int nsf = LS ? kf.ns : op.f2.ns, nsi = LS ? ki.ns : op.i2.ns;
@@ -201,6 +204,7 @@ __global__ void __launch_bounds__(512) k3_rows_inv(OpDev<T> op, const C_t<T>* __
                                                    const U* __restrict__ u, IO* __restrict__ y,
                                                    const int* __restrict__ skip) {
     using C = C_t<T>;
+    pdl_wait();
     if (skip && *skip) return;
     constexpr FftPlan ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan iv = LS ? ki : op.i1;
@@ -244,6 +248,7 @@ __global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict
                                                  const C_t<T>* __restrict__ chir, C_t<T>* __restrict__ vbuf,
                                                  const int* __restrict__ skip) {
     using C = C_t<T>;
+    pdl_wait();
     if (skip && *skip) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan f = LS ? kf : op.f1;
@@ -305,6 +310,255 @@ __global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict
     }
 }
 
+// ------------------------------------------------------------------ fast path
+// Grids with n = L / 2 exactly and L = 2^a in [256, 4096] (the padding is then exactly
+// half of every transform): the same passes with the compile-time stages of
+// fft_fast.cuh.  The zero inputs (index >= n) of the forward transforms and the
+// discarded outputs (index >= n) of the inverse ones are known at compile time.
+template <typename C, int L> constexpr int fast_tr() {
+    return tile_rows<C>() * (L / 16) <= kRowsMaxThreads ? tile_rows<C>() : kRowsMaxThreads / (L / 16);
+}
+template <int L> constexpr int tile_stride_c() { return L + (L >> 4) + 2; }
+
+// Asynchronous global -> shared copy of one complex value (no register staging), and the
+// wait for all of this thread's copies.
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* smem, const C* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(C) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Blocks per SM that the column pass should fit: all M1 = 1024 complex64 columns in one
+// wave of 152 SMs needs 7 (at most 72 registers per thread).
+template <typename C, int L> constexpr int k2_min_blocks() { return (sizeof(C) == 8 && L == 1024) ? 7 : 1; }
+
+// Transposed tile I/O of the row passes: thread (k0 = tid / TR, r = tid % TR) moves
+// elements k1 = k0 + it G, it < 16, of tile row r.
+template <typename C, int L, int TR, bool STORE>
+__device__ __forceinline__ void tile_io(C* tile, C* __restrict__ W, int c, int i2_0, int n2) {
+    constexpr int G = L / 16, Lp = tile_stride_c<L>();
+    const int r = threadIdx.x % TR, k0 = threadIdx.x / TR;
+    const int row = i2_0 + r;
+    C* t = tile + r * Lp + pidx(k0);
+    C* g = W + ((long)c * L + k0) * n2 + row;
+    const long gs = (long)G * n2;
+#pragma unroll
+    for (int it = 0; it < 16; it++) {
+        const int off = it * G + ((it * G) >> 4);
+        if constexpr (STORE) {
+            if (row < n2) g[it * gs] = t[off];
+        } else {
+            t[off] = row < n2 ? g[it * gs] : czero<C>();
+        }
+    }
+}
+
+template <typename T, typename IO, int L>
+__global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict__ u, const C_t<T>* __restrict__ chi,
+                                               C_t<T>* __restrict__ W, const int* __restrict__ skip) {
+    using C = C_t<T>;
+    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    using F0 = typename PlanStage<C, L, false, 0>::St;
+    pdl_wait();
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int rs = threadIdx.x / G, t = threadIdx.x % G;
+    const int c = blockIdx.y, i2_0 = blockIdx.x * TR, i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    C* buf = tile + rs * tile_stride_c<L>();
+    C x[16];
+    if (active) {
+        const long N = (long)n1 * op.n2;
+        const IO* ur = u + c * N + (long)i2 * n1 + t;
+        const C* cr = chi + (long)i2 * n1 + t;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int idx = F0::index(e);
+            x[e] = idx < n1 ? cmul(cvt<C>(ur[idx]), cr[idx]) : czero<C>();
+        }
+        F0::compute(x, t, op.tw1);
+        F0::store(buf, x, t);
+    }
+    __syncthreads();
+    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.tw1, active);
+    tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_fast(OpDev<T> op, C_t<T>* __restrict__ W,
+                                                                                 int stage_g, const int* __restrict__ skip) {
+    using C = C_t<T>;
+    constexpr int G = L / 16, n2 = L / 2, Q2 = L / 2 + 1, Lp = L + (L >> 4);
+    constexpr int nsf = P2<L>::fwd.ns, nsi = P2<L>::inv.ns;
+    using F0 = typename PlanStage<C, L, false, 0>::St;
+    using I0 = typename PlanStage<C, L, true, 0>::St;
+    using IL = typename PlanStage<C, L, true, nsi - 1>::St;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + Lp;
+    C* gs = buf1 + Lp;
+    const int comp = threadIdx.x >= G ? 1 : 0;
+    const int t = threadIdx.x - comp * G;
+    C* buf = comp ? buf1 : buf0;
+    const int k1 = blockIdx.x;
+    C* col = W + ((long)comp * op.M1 + k1) * n2 + t;
+    const int h1 = op.M1 >> 1;
+    const int k1q = k1 <= h1 ? k1 : op.M1 - k1;
+    const bool neg1 = k1 > h1;
+    const long plane = (long)op.Q1 * Q2;
+    const C* g = op.gq + (long)k1q * Q2;
+    if (stage_g) {   // the column's three quarter-spectrum rows (operator constants), issued
+                     // before the wait on the previous kernel; they land during the forward FFT
+        for (int e = threadIdx.x; e < 3 * Q2; e += 2 * G) {
+            const int pl = e / Q2, q = e - pl * Q2;
+            cp_async_elem(gs + e, g + pl * plane + q);
+        }
+    }
+    pdl_wait();
+    if (skip && *skip) {
+        cp_async_wait_all();
+        return;
+    }
+    C x[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int idx = F0::index(e);
+        x[e] = idx < n2 ? col[idx] : czero<C>();
+    }
+    F0::compute(x, t, op.tw2);
+    F0::store(buf, x, t);
+    __syncthreads();
+    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.tw2, true);
+    if (stage_g) {
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    {   // 2 x 2 Green-spectrum multiply at the first inverse stage's indices k2 = t + c
+        const long ps = stage_g ? (long)Q2 : plane;
+        const C* gsrc = stage_g ? gs : g;
+        const C* gdp = gsrc + comp * ps + t;     // k2 <= L/2: quarter index k2
+        const C* gop = gsrc + 2 * ps + t;
+        const C* gdm = gsrc + comp * ps - t;     // k2 > L/2: quarter index L - k2
+        const C* gom = gsrc + 2 * ps - t;
+        const C* a0 = buf0 + pidx(t);
+        const C* a1 = buf1 + pidx(t);
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int c = I0::index(e);
+            const C a = a0[c + (c >> 4)], b = a1[c + (c >> 4)];
+            C gd, go;
+            bool neg2;
+            if (c < L / 2) { gd = gdp[c]; go = gop[c]; neg2 = false; }
+            else { gd = gdm[L - c]; go = gom[L - c]; neg2 = c > L / 2 || t > 0; }
+            if (neg1 != neg2) { go.x = -go.x; go.y = -go.y; }
+            x[e] = comp == 0 ? cadd(cmul(gd, a), cmul(go, b)) : cadd(cmul(go, a), cmul(gd, b));
+        }
+    }
+    __syncthreads();
+    I0::compute(x, t, op.tw2);
+    I0::store(buf, x, t);
+    __syncthreads();
+    run_fast<C, L, true, 1, nsi - 1, false>(buf, x, t, op.tw2, true);
+    IL::load(buf, x, t);
+    IL::compute(x, t, op.tw2);
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int idx = IL::index(e);
+        if (idx < n2) col[idx] = x[e];
+    }
+}
+
+template <typename T, typename U, typename IO, int L>
+__global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __restrict__ W, const U* __restrict__ u,
+                                               IO* __restrict__ y, const int* __restrict__ skip) {
+    using C = C_t<T>;
+    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2, ns = P2<L>::inv.ns;
+    using IL = typename PlanStage<C, L, true, ns - 1>::St;
+    pdl_wait();
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int rs = threadIdx.x / G, t = threadIdx.x % G;
+    const int c = blockIdx.y, i2_0 = blockIdx.x * TR, i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    C* buf = tile + rs * tile_stride_c<L>();
+    const long off = c * ((long)n1 * op.n2) + (long)(active ? i2 : 0) * n1 + t;
+    U up[8];                    // u at this thread's output indices, loaded before the FFT
+#pragma unroll
+    for (int e = 0, q = 0; e < 16; e++)
+        if (IL::index(e) < n1) up[q++] = u[off + IL::index(e)];
+    tile_io<C, L, TR, false>(tile, const_cast<C*>(W), c, i2_0, op.n2);
+    __syncthreads();
+    C x[16];
+    run_fast<C, L, true, 0, ns - 1, false>(buf, x, t, op.tw1, active);
+    if (!active) return;
+    IL::load(buf, x, t);
+    IL::compute(x, t, op.tw1);
+#pragma unroll
+    for (int e = 0, q = 0; e < 16; e++) {
+        const int idx = IL::index(e);
+        if (idx < n1) y[off + idx] = csub(cvt<IO>(up[q++]), cvt<IO>(x[e]));
+    }
+}
+
+template <typename T, typename IO, int L>
+__global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict__ W, const IO* __restrict__ u,
+                                                 const C_t<T>* __restrict__ chir, C_t<T>* __restrict__ vbuf,
+                                                 const int* __restrict__ skip) {
+    using C = C_t<T>;
+    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    constexpr int nsi = P2<L>::inv.ns, nsf = P2<L>::fwd.ns;
+    using IL = typename PlanStage<C, L, true, nsi - 1>::St;
+    using F0 = typename PlanStage<C, L, false, 0>::St;
+    static_assert(IL::kR == F0::kR, "the inverse plan is the reversed forward plan");
+    pdl_wait();
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int rs = threadIdx.x / G, t = threadIdx.x % G;
+    const int c = blockIdx.y, i2_0 = blockIdx.x * TR, i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    C* buf = tile + rs * tile_stride_c<L>();
+    const long off = c * ((long)n1 * op.n2) + (long)(active ? i2 : 0) * n1 + t;
+    const C* cr = chir + (long)(active ? i2 : 0) * n1 + t;
+    C up[8], cp[8];             // u and chi' at this thread's indices, loaded before the FFT
+#pragma unroll
+    for (int e = 0, q = 0; e < 16; e++)
+        if (IL::index(e) < n1) { up[q] = cvt<C>(u[off + IL::index(e)]); cp[q] = cr[IL::index(e)]; q++; }
+    tile_io<C, L, TR, false>(tile, W, c, i2_0, op.n2);
+    __syncthreads();
+    C x[16];
+    run_fast<C, L, true, 0, nsi - 1, false>(buf, x, t, op.tw1, active);
+    if (active) {
+        IL::load(buf, x, t);
+        IL::compute(x, t, op.tw1);
+        // v = u - z (first product), kept for the final subtraction; then chi' v -> FFT
+#pragma unroll
+        for (int e = 0, q = 0; e < 16; e++) {
+            const int idx = IL::index(e);
+            if (idx < n1) {
+                const C v = csub(up[q], x[e]);
+                vbuf[off + idx] = v;
+                x[e] = cmul(v, cp[q]);
+                q++;
+            } else {
+                x[e] = czero<C>();
+            }
+        }
+    }
+    __syncthreads();            // every thread has read its last inverse stage from the tile
+    if (active) {
+        F0::compute(x, t, op.tw1);
+        F0::store(buf, x, t);
+    }
+    __syncthreads();
+    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.tw1, active);
+    tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
+}
+
 // --------------------------------------------------------------------- launch
 struct Launch { dim3 grid, block; size_t smem; };
 
@@ -333,7 +587,7 @@ inline void launch_kernel(K kernel, bool& attr_set, const Launch& l, cudaStream_
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
-    kernel<<<l.grid, l.block, l.smem, st>>>(args...);
+    launch_pdl(kernel, l.grid, l.block, l.smem, st, args...);
 }
 
 // Compile-time lengths with a dedicated instantiation; anything else takes the runtime plan.
@@ -349,8 +603,36 @@ inline void launch_kernel(K kernel, bool& attr_set, const Launch& l, cudaStream_
         default: DEFAULT; break;          \
     }
 
+// Grids on the fast path: n = L / 2 with L = 2^a in [256, 4096] (per direction).
+template <typename T> inline bool fast_rows(const OpDev<T>& v) {
+    return 2 * v.n1 == v.M1 && v.M1 >= 256 && v.M1 <= 4096 && (v.M1 & (v.M1 - 1)) == 0;
+}
+template <typename T> inline bool fast_cols(const OpDev<T>& v) {
+    return 2 * v.n2 == v.M2 && v.M2 >= 256 && v.M2 <= 4096 && (v.M2 & (v.M2 - 1)) == 0;
+}
+template <typename C, int L> inline Launch rows_launch_fast(int n2) {
+    constexpr int TR = fast_tr<C, L>();
+    return Launch{dim3((n2 + TR - 1) / TR, 2), dim3(TR * (L / 16)), (size_t)TR * tile_stride_c<L>() * sizeof(C)};
+}
+
+#define DIE_FAST_SWITCH(M, CASE)  \
+    switch (M) {                  \
+        case 256: CASE(256); break;   \
+        case 512: CASE(512); break;   \
+        case 1024: CASE(1024); break; \
+        case 2048: CASE(2048); break; \
+        case 4096: CASE(4096); break; \
+        default: break;               \
+    }
+
 template <typename T, typename IO>
 inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st) {
+    if (fast_rows(v)) {
+#define K1F_CASE(LSV) { static bool a_ = false; launch_kernel(k1_fast<T, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, u, chi, W, skip); }
+        DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1F_CASE));
+#undef K1F_CASE
+        return;
+    }
     const Launch l = rows_launch(v);
 #define K1_CASE(LSV) { static bool a_ = false; launch_kernel(k1_rows_fwd<T, IO, 16, LSV>, a_, l, st, v, u, chi, W, skip); }
 #define K1_DEF { static bool a16 = false, a12 = false;                                                     \
@@ -365,6 +647,12 @@ template <typename T>
 inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_t st) {
     int sg = 0;
     const Launch l = cols_launch(v, &sg);
+    if (fast_cols(v)) {
+#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast<T, LSV>, a_, l, st, v, W, sg, skip); }
+        DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
+#undef K2F_CASE
+        return;
+    }
 #define K2_CASE(LSV) { static bool a_ = false; launch_kernel(k2_cols<T, 16, LSV>, a_, l, st, v, W, sg, skip); }
 #define K2_DEF { static bool a16 = false, a12 = false;                                            \
                  if (v.f2.ept == 16) launch_kernel(k2_cols<T, 16, 0>, a16, l, st, v, W, sg, skip); \
@@ -376,6 +664,12 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
 
 template <typename T, typename U, typename IO>
 inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st) {
+    if (fast_rows(v)) {
+#define K3F_CASE(LSV) { static bool a_ = false; launch_kernel(k3_fast<T, U, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, W, u, y, skip); }
+        DIE_PROF(PK_ROWS_INV, st, DIE_FAST_SWITCH(v.M1, K3F_CASE));
+#undef K3F_CASE
+        return;
+    }
     const Launch l = rows_launch(v);
 #define K3_CASE(LSV) { static bool a_ = false; launch_kernel(k3_rows_inv<T, U, IO, 16, LSV>, a_, l, st, v, W, u, y, skip); }
 #define K3_DEF { static bool a16 = false, a12 = false;                                                    \
@@ -389,6 +683,12 @@ inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, con
 template <typename T, typename IO>
 inline void launch_k3k1(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
                         cudaStream_t st) {
+    if (fast_rows(v)) {
+#define KKF_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_fast<T, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, W, u, chir, vb, skip); }
+        DIE_PROF(PK_ROWS_INV_FWD, st, DIE_FAST_SWITCH(v.M1, KKF_CASE));
+#undef KKF_CASE
+        return;
+    }
     const Launch l = rows_launch(v);
 #define KK_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_rows<T, IO, 16, LSV>, a_, l, st, v, W, u, chir, vb, skip); }
 #define KK_DEF { static bool a16 = false, a12 = false;                                                        \

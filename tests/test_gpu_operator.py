@@ -64,7 +64,7 @@ def test_apply_explicit_fft_sizes(n1, n2, M):
     assert rel(op.apply_regularized(xt).cpu().numpy(), ref.apply_regularized(x)) < FP64_TOL
 
 
-@pytest.mark.parametrize("n", [64, 96, 128, 200])
+@pytest.mark.parametrize("n", [64, 96, 128, 200, 256])
 def test_apply_matches_fft_oracle(n):
     p = W.core_shell(n, side=n / 64.0, r_core=1.5 * n / 512, r_shell=2.5 * n / 512)
     rng = W.rng_for(102, n)
@@ -76,6 +76,40 @@ def test_apply_matches_fft_oracle(n):
     assert rel(op.apply_regularized(xt).cpu().numpy(), ref.apply_regularized(x)) < FP64_TOL
     op32 = die.Operator(p.eps_r, p.h, prec=die.DIE_FP32_INNER)
     assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), ref.apply_regularized(x)) < C64_TOL
+
+
+# Grids with n = M/2 and M = 2^a >= 256 along a direction take the compile-time FFT
+# kernels there; these mix them with the general kernels in the other direction.
+@pytest.mark.parametrize("n1,n2", [(128, 200), (200, 128), (256, 64), (128, 1024)])
+def test_apply_mixed_fast_and_general_passes(n1, n2):
+    rng = W.rng_for(105, n1 * 10000 + n2)
+    eps = W.random_field(rng, n1, n2, lo=1.0, hi=9.0, loss=0.5)
+    h = 2.0 / max(n1, n2)
+    x = W.random_vector(rng, n1, n2)
+    ref = fftmv.FFTOperator(eps, h)
+    op = die.Operator(eps, h)
+    xt = dev(x)
+    assert rel(op.apply(xt).cpu().numpy(), ref.apply(x)) < FP64_TOL
+    assert rel(op.apply_regularized(xt).cpu().numpy(), ref.apply_regularized(x)) < FP64_TOL
+    op32 = die.Operator(eps, h, prec=die.DIE_FP32_INNER)
+    x32 = dev(x, torch.complex64)
+    assert rel(op32.apply(x32).cpu().numpy(), ref.apply(x)) < C64_TOL
+    assert rel(op32.apply_regularized(x32).cpu().numpy(), ref.apply_regularized(x)) < C64_TOL
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_large_grids_match_fft_oracle(n):
+    """The compile-time kernels at L = 2048 and 4096 (the largest transform)."""
+    p = W.core_shell(n, side=n / 64.0, r_core=1.5 * n / 512, r_shell=2.5 * n / 512)
+    rng = W.rng_for(106, n)
+    x = W.random_vector(rng, n, n)
+    ref = fftmv.FFTOperator(p.eps_r, p.h, workers=8)
+    yr = ref.apply_regularized(x)
+    op = die.Operator(p.eps_r, p.h)
+    assert rel(op.apply_regularized(dev(x)).cpu().numpy(), yr) < FP64_TOL
+    del op
+    op32 = die.Operator(p.eps_r, p.h, prec=die.DIE_FP32_INNER)
+    assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), yr) < C64_TOL
 
 
 def test_in_place_apply():
@@ -111,7 +145,10 @@ def test_full_size_core_shell_512():
     exact = rows.rows_apply(dense.contrast(p.eps_r), x, p.h, idx)
     assert np.max(np.abs(got - exact)) / np.max(np.abs(y)) < FP64_TOL
     yr = op.apply_regularized(dev(x)).cpu().numpy()
-    assert rel(yr, ref.apply_regularized(x)) < FP64_TOL
+    yref = ref.apply_regularized(x)
+    assert rel(yr, yref) < FP64_TOL
+    op32 = die.Operator(p.eps_r, p.h, prec=die.DIE_FP32_INNER)
+    assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), yref) < C64_TOL
 
 
 def test_singular_permittivity_rejected():
