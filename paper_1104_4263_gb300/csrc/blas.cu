@@ -278,15 +278,25 @@ __global__ void __launch_bounds__(kRedThreads, 2) proj32_kernel(const float2* __
 __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2* __restrict__ V, long ldv, int r,
                                                                     const float2* __restrict__ cf,
                                                                     const float2* x, float2* z, long n,
-                                                                    const int* skip) {
+                                                                    const int* skip, double2* w, const double* inv) {
     pdl_wait();
     if (skip && *skip) return;
     __shared__ float2 cs[kMaxBasis];
     for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = __ldcg(&cf[i]);
     __syncthreads();
+    const double sc = inv ? *inv : 1.0;
     const long stride = (long)gridDim.x * blockDim.x;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        float2 acc = x[idx];
+        float2 acc;
+        if (inv) {                          // normalise the FP64 vector, take its complex64 copy
+            double2 u = w[idx];
+            u.x *= sc;
+            u.y *= sc;
+            w[idx] = u;
+            acc = make_float2((float)u.x, (float)u.y);
+        } else {
+            acc = x[idx];
+        }
         float ex = 0, ey = 0;
         int i = 0;
 #pragma unroll 4
@@ -378,6 +388,107 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
                 *dec.skip2 = (dec.done && *dec.done) || !r;
             }
             if (dec.inv && !r) *dec.inv = inv_norm(tot);
+        }
+    }
+}
+
+// Gram-Schmidt update w = base - V c with ||w||^2 and the DGKS decision (as
+// basis_axpy_kernel<double2, true> with sign -1), and the deflation projections
+// V32^* w folded in: NGD groups of 8 complex64 basis vectors, FP32 products and
+// in-block sums (the FP32 pipe and the spare memory bandwidth of this FP64-bound
+// pass).  Reduction vector 0 is ||w||^2, vectors 1 .. r the projections.  The last
+// block writes ||w||^2 to nrm2 and, when no second pass follows, 1 / ||w|| to dec.inv
+// and cf = M32 (V32^* w / ||w||) to dp.cf.
+template <int NGD>
+__global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const double2* __restrict__ V, long ldv, int k,
+                                                                      const double2* __restrict__ coef,
+                                                                      const double2* base, double2* out, long n,
+                                                                      double2* nrm2, Dgks dec, int has_dec,
+                                                                      DeflProj dp, RedScratch rs, const int* skip,
+                                                                      int live) {
+    pdl_wait();
+    const bool off = skip && *skip;
+    if (off && !live) return;
+    __shared__ double2 cs[kMaxBasis];
+    __shared__ double csn[kMaxBasis];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double2 c = make_double2(-coef[i].x, -coef[i].y);
+        cs[i] = c;
+        csn[i] = -c.y;
+    }
+    __syncthreads();
+    double nacc = 0;
+    float dacc[NGD][16];
+#pragma unroll
+    for (int g = 0; g < NGD; g++)
+#pragma unroll
+        for (int q = 0; q < 16; q++) dacc[g][q] = 0.f;
+    const long stride = (long)gridDim.x * blockDim.x;
+    const long nn = off ? 0 : n;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nn; idx += stride) {
+        double x0 = 0, y0 = 0;
+        if (base) { const double2 bv = base[idx]; x0 = bv.x; y0 = bv.y; }
+#pragma unroll 4
+        for (int i = 0; i < k; i++) {
+            const double2 a = V[(long)i * ldv + idx], c = cs[i];
+            x0 = fma(a.x, c.x, x0); x0 = fma(a.y, csn[i], x0);
+            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+        }
+        const double2 o = make_double2(x0, y0);
+        out[idx] = o;
+        nacc = fma(o.x, o.x, nacc);
+        nacc = fma(o.y, o.y, nacc);
+        const float2 of = make_float2((float)o.x, (float)o.y);
+#pragma unroll
+        for (int g = 0; g < NGD; g++) {
+            float2 a[8];
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                const int i = 8 * g + v;
+                a[v] = i < dp.r ? dp.V32[(long)i * dp.ld + idx] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int v = 0; v < 8; v++) conj_mac(a[v], of, dacc[g][2 * v], dacc[g][2 * v + 1]);
+        }
+    }
+    {
+        double acc[2] = {nacc, 0.0};
+        __shared__ double red[(kRedThreads / 32) * 2];
+        block_partials<double, 2, 1>(acc, red, 0, rs);
+    }
+    __shared__ float redf[(kRedThreads / 32) * 16];
+#pragma unroll
+    for (int g = 0; g < NGD; g++) block_partials<float, 16, 8>(dacc[g], redf, 1 + 8 * g, rs);
+    if (reduce_partials(rs, 1 + dp.r, dp.s)) {
+        __shared__ float s_iv;
+        __shared__ int s_fin;
+        if (threadIdx.x == 0) {
+            const double tot = __ldcg(&dp.s[0].x);
+            *nrm2 = make_double2(tot, 0.0);
+            int r = 0;
+            if (has_dec) {
+                r = dec.always || tot < dec.eta2 * dec.before2->x;
+                *dec.reorth = r;
+                *dec.skip2 = (dec.done && *dec.done) || !r;
+            }
+            const double iv = inv_norm(tot);
+            if (dec.inv && !r) *dec.inv = iv;
+            s_iv = (float)iv;
+            s_fin = !r;
+        }
+        __syncthreads();
+        if (s_fin) {
+            for (int i = threadIdx.x; i < dp.r; i += blockDim.x) {
+                float cx = 0, cy = 0;
+                for (int q = 0; q < dp.r; q++) {
+                    const float2 m = dp.M32[(long)q * dp.r + i];
+                    const double2 sq = __ldcg(&dp.s[1 + q]);
+                    const float sx = (float)sq.x * s_iv, sy = (float)sq.y * s_iv;
+                    cx = fmaf(m.x, sx, cx); cx = fmaf(-m.y, sy, cx);
+                    cy = fmaf(m.x, sy, cy); cy = fmaf(m.y, sx, cy);
+                }
+                dp.cf[i] = make_float2(cx, cy);
+            }
         }
     }
 }
@@ -564,16 +675,35 @@ die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, co
     return DIE_OK;
 }
 die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
-                           const int* skip, cudaStream_t st) {
-    if (r > kMaxBasis || r < 1) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(defl_update32_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, V, ldv, r, cf, x, z, n, skip));
+                           const int* skip, cudaStream_t st, double2* w, const double* inv) {
+    if (r > kMaxBasis || r < 1 || (inv && !w)) return DIE_EINVAL;
+    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(defl_update32_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, V, ldv, r, cf, x, z, n, skip, w, inv));
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+// Update pass with the deflation projections folded in (see cgs_update_defl_kernel).
+static die_status k_update_defl(const double2* V, long ldv, int k, const double2* coef, double2* w, long n,
+                                double2* nrm2, const Dgks& dec, int has_dec, const DeflProj& dp, const RedScratch& rs,
+                                const int* skip, cudaStream_t st, bool live) {
+    if (k > kMaxBasis || k < 0 || dp.r < 1 || dp.r > kDeflFoldMax) return DIE_EINVAL;
+    const int ng = (dp.r + 7) / 8;
+#define UPD_CASE(NG) DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(cgs_update_defl_kernel<NG>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, \
+                              V, ldv, k, coef, (const double2*)w, w, n, nrm2, dec, has_dec, dp, rs, skip, live ? 1 : 0))
+    switch (ng) {
+        case 1: UPD_CASE(1); break;
+        case 2: UPD_CASE(2); break;
+        case 3: UPD_CASE(3); break;
+        default: UPD_CASE(4); break;
+    }
+#undef UPD_CASE
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
                     int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st,
-                    double* inv) {
+                    double* inv, const DeflProj* dp) {
     Dgks dec;
     dec.before2 = h1 + nv;
     dec.reorth = reorth;
@@ -583,13 +713,17 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.always = eta2 >= 1.0 ? 1 : 0;
     dec.eta2 = eta2;
     DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true));
-    DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true));
+    if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true));
+    else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true));
     Dgks last;                       // second pass: no decision, only the scale factor
     last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;
     die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st);
     g_prof_override = PK_UPDATE_REORTH;
-    if (s == DIE_OK) s = k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st);
+    if (s == DIE_OK) {
+        s = dp ? k_update_defl(V, ldv, nv, h2, w, n, nrm + 1, last, 0, *dp, rs, skip2, st, false)
+               : k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st);
+    }
     g_prof_override = -1;
     return s;
 }

@@ -93,6 +93,44 @@ struct FStage {
             }
     }
 
+    // The same stage on two independent transforms (x0, x1) at the same indices, with the
+    // twiddles loaded once for both.
+    __device__ static __forceinline__ void compute2(V (&x0)[16], V (&x1)[16], int t, const V* __restrict__ tw) {
+        if constexpr (NS > 1) {
+            constexpr int step = L / (NS * R);
+            if constexpr (kUniformK) {
+                const int k = t & (NS - 1);
+#pragma unroll
+                for (int r = 1; r < R; r++) {
+                    V w = __ldg(&tw[step * r * k]);
+                    if (INV) w.y = -w.y;
+#pragma unroll
+                    for (int b = 0; b < B; b++) {
+                        x0[b * R + r] = cmul(x0[b * R + r], w);
+                        x1[b * R + r] = cmul(x1[b * R + r], w);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; b++) {
+                    const int k = t + b * G;
+#pragma unroll
+                    for (int r = 1; r < R; r++) {
+                        V w = __ldg(&tw[step * r * k]);
+                        if (INV) w.y = -w.y;
+                        x0[b * R + r] = cmul(x0[b * R + r], w);
+                        x1[b * R + r] = cmul(x1[b * R + r], w);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; b++) {
+            dft<V, R, INV>(&x0[b * R]);
+            dft<V, R, INV>(&x1[b * R]);
+        }
+    }
+
     // Natural index of register e in the stage's input (first stage) or output (last stage).
     static constexpr int index(int e) { return (e / R) * G + (e % R) * LR; }
 };
@@ -128,6 +166,22 @@ __device__ __forceinline__ void run_fast(V* buf, V (&x)[16], int t, const V* tw,
         }
         __syncthreads();
         run_fast<V, L, INV, S0 + 1, S1, false>(buf, x, t, tw, active);
+    }
+}
+
+// run_fast on two transforms held by the same threads, in buffers buf0 and buf1.
+template <typename V, int L, bool INV, int S0, int S1>
+__device__ __forceinline__ void run_fast2(V* buf0, V* buf1, V (&x0)[16], V (&x1)[16], int t, const V* tw) {
+    if constexpr (S0 < S1) {
+        using St = typename PlanStage<V, L, INV, S0>::St;
+        St::load(buf0, x0, t);
+        St::load(buf1, x1, t);
+        __syncthreads();
+        St::compute2(x0, x1, t, tw);
+        St::store(buf0, x0, t);
+        St::store(buf1, x1, t);
+        __syncthreads();
+        run_fast2<V, L, INV, S0 + 1, S1>(buf0, buf1, x0, x1, t, tw);
     }
 }
 

@@ -291,6 +291,19 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     // and keep its complex64 copy.
     const bool defl32 = defl && mixed;
     float2* v32 = defl32 ? c->v32 : nullptr;
+    // For r <= kDeflFoldMax the deflation projections of v_{j+1} are folded into the
+    // Gram-Schmidt update of step j (which produces cf for step j+1), and the deflation
+    // update of step j+1 normalises v_{j+1}; otherwise they run as their own pass.
+    const bool fold = defl32 && defl->r <= kDeflFoldMax;
+    DeflProj dp;
+    if (fold) {
+        dp.V32 = defl->V32;
+        dp.ld = n;
+        dp.r = defl->r;
+        dp.M32 = defl->M32;
+        dp.s = defl->s;
+        dp.cf = defl->c32;
+    }
     // the complex64 deflation basis is read twice per Arnoldi step: keep it in L2
     L2Pin pin(st, defl32 ? defl->V32 : nullptr, defl32 ? (size_t)defl->r * n * sizeof(float2) : 0);
     if (bnorm == 0.0) {
@@ -313,6 +326,9 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (rel <= o->tol) { status = DIE_OK; break; }
         if (iters >= o->max_iters) break;
         DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32));
+        if (fold)   // cf for v_0
+            DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, defl->s, defl->M32, defl->c32,
+                             defl->rs, nullptr, st));
         DIE_TRY(k_gmres_init(S, scal, st));
         const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
         S.jmax = jmax;
@@ -325,7 +341,13 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
             double2* w = V + (long)(j + 1) * ldv;
             const double* inv_prev = j > 0 ? S.inv + (j - 1) : nullptr;
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j], st));
-            if (defl32) {
+            if (fold) {
+                DIE_TRY(k_defl_update32(defl->V32, n, defl->r, defl->c32, c->v32, c->z32, n, S.done, st,
+                                        j > 0 ? vj : nullptr, inv_prev));
+                if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
+                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
+                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
+            } else if (defl32) {
                 DIE_TRY(defl_apply32(defl, c->v32, j > 0 ? vj : nullptr, inv_prev, c->z32, S.done, st, true));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
                 DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
@@ -342,7 +364,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
             }
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
             DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1 + (long)j * (m + 3), S.h2 + (long)j * (m + 3), S.nrm + 2 * j,
-                             S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j));
+                             S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j, fold ? &dp : nullptr));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
             DIE_CUDA_TRY(cudaEventRecord(c->fork, st));
             DIE_CUDA_TRY(cudaStreamWaitEvent(side, c->fork, 0));

@@ -44,6 +44,20 @@ struct Dgks {
     double eta2 = 0.5;
 };
 
+// Deflation projections folded into a Gram-Schmidt update (FP32-inner deflated solves):
+// while the update kernel writes the new vector w, it also accumulates V32^* w in FP32
+// (w rounded to complex64); the block that finishes its sums forms
+// cf = M32 (V32^* w / ||w||) for the deflation update of the next Arnoldi step.
+struct DeflProj {
+    const float2* V32 = nullptr;   // r complex64 basis vectors, vector i at V32 + i * ld
+    long ld = 0;
+    int r = 0;                     // 1 <= r <= kDeflFoldMax
+    const float2* M32 = nullptr;   // r x r, column-major (M = T^-1 - I in complex64)
+    double2* s = nullptr;          // 1 + r scratch: ||w||^2, then V32^* w
+    float2* cf = nullptr;          // r coefficients (complex64)
+};
+constexpr int kDeflFoldMax = 32;   // largest r folded into the update
+
 // State of one GMRES cycle on the device (all FP64).  The per-step arrays (projections,
 // norms, DGKS flag, scale factor) have one slot per Arnoldi step, so that the Givens
 // step of step j, which runs on a side stream, reads values that step j+1 does not
@@ -92,18 +106,21 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
 // z = x + V (M s); M r x r column-major; s the projections V^* x.  z may equal x.
 die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
                          double2* z, long n, const int* skip, cudaStream_t st);
-// All-complex64 deflation update (FP32-inner solves): z = x + V cf, cf from k_dots32.
+// All-complex64 deflation update (FP32-inner solves): z = x + V cf, cf from k_dots32 or
+// from a folded update.  With inv != NULL the input is formed from the FP64 vector w:
+// w *= *inv (written back) and x = complex64(w) (x itself is then not read).
 die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
-                           const int* skip, cudaStream_t st);
+                           const int* skip, cudaStream_t st, double2* w = nullptr, const double* inv = nullptr);
 
 // Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion (done is a
 // live flag, see above):
 // h1 = V^* w (||w||^2 in h1[nv]); w -= V h1 (||w||^2 -> nrm[0]); if ||w||^2 < eta2
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
 // inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).
+// dp != NULL folds the deflation projections of the final w into the update passes.
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2,
                     double2* nrm, int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs,
-                    cudaStream_t st, double* inv = nullptr);
+                    cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr);
 
 // v *= 1 / sqrt(re(*nrm2)) if positive; v *= *inv.  v32 != NULL also receives the
 // scaled vector rounded to complex64.

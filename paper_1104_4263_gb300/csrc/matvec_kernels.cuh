@@ -471,6 +471,101 @@ __global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_f
     }
 }
 
+// Complex64 column pass with both components in the same thread (G threads per column):
+// the last forward stage leaves each thread's values at the indices where the first
+// inverse stage (same radix: the inverse plan is the reversed forward plan) wants them,
+// so the 2 x 2 Green multiply is done in registers between the two, with no shared-
+// memory round trip, and every twiddle serves both components.
+template <typename T, int L>
+__global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T> op, C_t<T>* __restrict__ W,
+                                                                        int stage_g, const int* __restrict__ skip) {
+    using C = C_t<T>;
+    constexpr int G = L / 16, n2 = L / 2, Q2 = L / 2 + 1, Lp = L + (L >> 4);
+    constexpr int nsf = P2<L>::fwd.ns, nsi = P2<L>::inv.ns;
+    using F0 = typename PlanStage<C, L, false, 0>::St;
+    using FL = typename PlanStage<C, L, false, nsf - 1>::St;
+    using I0 = typename PlanStage<C, L, true, 0>::St;
+    using IL = typename PlanStage<C, L, true, nsi - 1>::St;
+    static_assert(FL::kR == I0::kR, "the inverse plan is the reversed forward plan");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + Lp;
+    C* gs = buf1 + Lp;
+    const int t = threadIdx.x;
+    const int k1 = blockIdx.x;
+    C* col0 = W + (long)k1 * n2 + t;
+    C* col1 = W + ((long)op.M1 + k1) * n2 + t;
+    const int h1 = op.M1 >> 1;
+    const int k1q = k1 <= h1 ? k1 : op.M1 - k1;
+    const bool neg1 = k1 > h1;
+    const long plane = (long)op.Q1 * Q2;
+    const C* g = op.gq + (long)k1q * Q2;
+    if (stage_g) {   // the column's three quarter-spectrum rows (operator constants), issued
+                     // before the wait on the previous kernel; they land during the forward FFT
+        for (int e = t; e < 3 * Q2; e += G) {
+            const int pl = e / Q2, q = e - pl * Q2;
+            cp_async_elem(gs + e, g + pl * plane + q);
+        }
+    }
+    pdl_wait();
+    if (skip && *skip) {
+        cp_async_wait_all();
+        return;
+    }
+    C x0[16], x1[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int idx = F0::index(e);
+        x0[e] = idx < n2 ? col0[idx] : czero<C>();
+        x1[e] = idx < n2 ? col1[idx] : czero<C>();
+    }
+    F0::compute2(x0, x1, t, op.tw2);
+    F0::store(buf0, x0, t);
+    F0::store(buf1, x1, t);
+    __syncthreads();
+    run_fast2<C, L, false, 1, nsf - 1>(buf0, buf1, x0, x1, t, op.tw2);
+    FL::load(buf0, x0, t);
+    FL::load(buf1, x1, t);
+    FL::compute2(x0, x1, t, op.tw2);
+    if (stage_g) cp_async_wait_all();
+    __syncthreads();             // spectra visible; every thread has read its last forward stage
+    {   // 2 x 2 Green-spectrum multiply at k2 = t + c (c = I0::index(e))
+        const long ps = stage_g ? (long)Q2 : plane;
+        const C* gsrc = stage_g ? gs : g;
+        const C* g11p = gsrc + t;           // k2 <= L/2: quarter index k2
+        const C* g22p = gsrc + ps + t;
+        const C* g12p = gsrc + 2 * ps + t;
+        const C* g11m = gsrc - t;           // k2 > L/2: quarter index L - k2
+        const C* g22m = gsrc + ps - t;
+        const C* g12m = gsrc + 2 * ps - t;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int c = I0::index(e);
+            C a, b, go;
+            bool neg2;
+            if (c < L / 2) { a = g11p[c]; b = g22p[c]; go = g12p[c]; neg2 = false; }
+            else { a = g11m[L - c]; b = g22m[L - c]; go = g12m[L - c]; neg2 = c > L / 2 || t > 0; }
+            if (neg1 != neg2) { go.x = -go.x; go.y = -go.y; }
+            const C u0 = x0[e], u1 = x1[e];
+            x0[e] = cadd(cmul(a, u0), cmul(go, u1));
+            x1[e] = cadd(cmul(go, u0), cmul(b, u1));
+        }
+    }
+    I0::compute2(x0, x1, t, op.tw2);
+    I0::store(buf0, x0, t);
+    I0::store(buf1, x1, t);
+    __syncthreads();
+    run_fast2<C, L, true, 1, nsi - 1>(buf0, buf1, x0, x1, t, op.tw2);
+    IL::load(buf0, x0, t);
+    IL::load(buf1, x1, t);
+    IL::compute2(x0, x1, t, op.tw2);
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int idx = IL::index(e);
+        if (idx < n2) { col0[idx] = x0[e]; col1[idx] = x1[e]; }
+    }
+}
+
 template <typename T, typename U, typename IO, int L>
 __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __restrict__ W, const U* __restrict__ u,
                                                IO* __restrict__ y, const int* __restrict__ skip) {
@@ -648,9 +743,16 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
     int sg = 0;
     const Launch l = cols_launch(v, &sg);
     if (fast_cols(v)) {
-#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast<T, LSV>, a_, l, st, v, W, sg, skip); }
-        DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
+        if constexpr (sizeof(C_t<T>) == 8) {     // complex64: both components per thread
+            const Launch l2{l.grid, dim3(v.M2 / 16), l.smem};
+#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast2<T, LSV>, a_, l2, st, v, W, sg, skip); }
+            DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
 #undef K2F_CASE
+        } else {
+#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast<T, LSV>, a_, l, st, v, W, sg, skip); }
+            DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
+#undef K2F_CASE
+        }
         return;
     }
 #define K2_CASE(LSV) { static bool a_ = false; launch_kernel(k2_cols<T, 16, LSV>, a_, l, st, v, W, sg, skip); }
