@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kRedThreads) proj_kernel(const VT* __restrict_
     constexpr int K = 2 * GV;
     __shared__ A red[(kRedThreads / 32) * K];
     pdl_wait();
-    const bool off = skip && *skip;
+    const bool off = block_flag(skip);
     if (off && !live) return;
     const int nvt = nv + (with_norm ? 1 : 0);
     for (int g0 = 0; g0 < nvt; g0 += GV) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) proj32_kernel(const float2* __
     constexpr int GV = 16, K = 2 * GV;     // 16 vectors per pass: 32 running sums, 16 loads in flight
     __shared__ float red[(kRedThreads / 32) * K];
     pdl_wait();
-    const bool off = skip && *skip;
+    const bool off = block_flag(skip);
     if (off && !live) return;
     const double sc = inv ? *inv : 1.0;
     for (int g0 = 0; g0 < nv; g0 += GV) {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2
                                                                     const float2* x, float2* z, long n,
                                                                     const int* skip, double2* w, const double* inv) {
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     __shared__ float2 cs[kMaxBasis];
     for (int i = threadIdx.x; i < r; i += blockDim.x) cs[i] = __ldcg(&cf[i]);
     __syncthreads();
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
                                                                  int live) {
     using A = typename acc_of<VT>::type;
     pdl_wait();
-    const bool off = skip && *skip;
+    const bool off = block_flag(skip);
     if (off && !(NORM && live)) return;
     __shared__ VT cs[kMaxBasis];
     __shared__ A csn[kMaxBasis];            // -Im(c): every step below is a plain FMA
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
                                                                       DeflProj dp, RedScratch rs, const int* skip,
                                                                       int live) {
     pdl_wait();
-    const bool off = skip && *skip;
+    const bool off = block_flag(skip);
     if (off && !live) return;
     __shared__ double2 cs[kMaxBasis];
     __shared__ double csn[kMaxBasis];
@@ -570,7 +570,7 @@ __device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float
 
 __global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32) {
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     __shared__ double s_inv;
     if (threadIdx.x == 0) s_inv = inv_norm(nrm2->x);
     __syncthreads();
@@ -579,7 +579,7 @@ __global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, c
 
 __global__ void scale_by_kernel(double2* v, long n, const double* inv, const int* skip, float2* v32) {
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     scale_rows(v, n, *inv, v32);
 }
 

@@ -66,6 +66,17 @@ __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : 
 // normal launch pdl_wait is a no-op.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// A skip flag's value for the whole block: thread 0 reads it once and the block shares
+// it.  A "live" flag (one that another stream may set while the kernel runs) read by
+// every thread could otherwise split a block between threads that skip and threads that
+// reach a barrier.
+__device__ __forceinline__ bool block_flag(const int* flag) {
+    __shared__ int s_flag;
+    if (threadIdx.x == 0) s_flag = flag ? *(const volatile int*)flag : 0;
+    __syncthreads();
+    return s_flag != 0;
+}
+
 bool pdl_enabled();   // false when the environment sets DIE_PDL=0
 
 template <typename... KArgs, typename... Args>

@@ -295,6 +295,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     // Gram-Schmidt update of step j (which produces cf for step j+1), and the deflation
     // update of step j+1 normalises v_{j+1}; otherwise they run as their own pass.
     const bool fold = defl32 && defl->r <= kDeflFoldMax;
+    const bool fold_product = fold && defl_product_ok(op);   // deflation inside the first row pass
     DeflProj dp;
     if (fold) {
         dp.V32 = defl->V32;
@@ -341,7 +342,18 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
             double2* w = V + (long)(j + 1) * ldv;
             const double* inv_prev = j > 0 ? S.inv + (j - 1) : nullptr;
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j], st));
-            if (fold) {
+            if (fold_product) {
+                DeflIn din;
+                din.V32 = defl->V32;
+                din.ld = n;
+                din.r = defl->r;
+                din.cf = defl->c32;
+                din.x = c->v32;
+                din.w = j > 0 ? vj : nullptr;
+                din.inv = inv_prev;
+                if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
+                DIE_TRY(apply_defl_xy(op, din, c->z32, w, reg, S.done, st));
+            } else if (fold) {
                 DIE_TRY(k_defl_update32(defl->V32, n, defl->r, defl->c32, c->v32, c->z32, n, S.done, st,
                                         j > 0 ? vj : nullptr, inv_prev));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));

@@ -16,4 +16,28 @@ template die_status apply_op_skip_xy<float, float2, double2>(dieop_s*, Contrast,
 template die_status apply_reg_skip_xy<float, float2, double2>(dieop_s*, const float2*, double2*, const int*,
                                                               cudaStream_t);
 
+bool defl_product_ok(const dieop_s* op) { return fast_rows(view_f(op)); }
+
+die_status apply_defl_xy(dieop_s* op, const DeflIn& d, float2* z, double2* y, bool reg, const int* skip,
+                         cudaStream_t st) {
+    const OpDev<float> v = view_f(op);
+    if (!fast_rows(v) || d.r < 1 || d.r > 32 || !d.V32 || !d.cf || (!d.w && !d.x) || (d.w && !d.inv))
+        return DIE_EINVAL;
+    float2* W = reinterpret_cast<float2*>(op->ws.W);
+    float2* vb = reinterpret_cast<float2*>(op->ws.v);
+#define K1D_CASE(LSV) { static bool a_ = false; launch_kernel(k1_defl_fast<LSV>, a_, rows_launch_fast<float2, LSV>(v.n2), st, v, d, op->chi_f, z, W, skip); }
+    DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1D_CASE));
+#undef K1D_CASE
+    launch_k2<float>(v, W, skip, st);
+    if (reg) {
+        launch_k3k1<float, float2>(v, W, z, op->chir_f, vb, skip, st);
+        launch_k2<float>(v, W, skip, st);
+        launch_k3<float, float2, double2>(v, W, vb, y, skip, st);
+    } else {
+        launch_k3<float, float2, double2>(v, W, z, y, skip, st);
+    }
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
 }  // namespace die

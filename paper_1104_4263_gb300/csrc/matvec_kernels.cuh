@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(512) k1_rows_fwd(OpDev<T> op, const IO* __rest
                                                    const int* __restrict__ skip) {
     using C = C_t<T>;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false);
     const FftPlan pl = LS ? kf : op.f1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__
                                                const int* __restrict__ skip) {
     using C = C_t<T>;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const int nsf = LS ? kf.ns : op.f2.ns, nsi = LS ? ki.ns : op.i2.ns;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(512) k3_rows_inv(OpDev<T> op, const C_t<T>* __
                                                    const int* __restrict__ skip) {
     using C = C_t<T>;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     constexpr FftPlan ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan iv = LS ? ki : op.i1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict
                                                  const int* __restrict__ skip) {
     using C = C_t<T>;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan f = LS ? kf : op.f1;
     const FftPlan iv = LS ? ki : op.i1;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
     constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
     using F0 = typename PlanStage<C, L, false, 0>::St;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -378,6 +378,93 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
         for (int e = 0; e < 16; e++) {
             const int idx = F0::index(e);
             x[e] = idx < n1 ? cmul(cvt<C>(ur[idx]), cr[idx]) : czero<C>();
+        }
+        F0::compute(x, t, op.tw1);
+        F0::store(buf, x, t);
+    }
+    __syncthreads();
+    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.tw1, active);
+    tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
+}
+
+// First row pass of a deflated FP32-inner product (complex64): per element
+// z = v + sum_i V32_i cf_i (v = w / ||w|| written back to the FP64 Arnoldi vector, or
+// the complex64 x), stored to zout for the later passes, then chi * z and the forward
+// row transform as in k1_fast.  The basis loads go four vectors (32 loads) at a time.
+template <int L>
+__global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, const float2* __restrict__ chi,
+                                                    float2* __restrict__ zout, float2* __restrict__ W,
+                                                    const int* __restrict__ skip) {
+    using C = float2;
+    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    using F0 = typename PlanStage<C, L, false, 0>::St;
+    __shared__ float2 cs[32];
+    pdl_wait();
+    if (block_flag(skip)) return;
+    for (int i = threadIdx.x; i < d.r; i += blockDim.x) cs[i] = __ldcg(&d.cf[i]);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int rs = threadIdx.x / G, t = threadIdx.x % G;
+    const int c = blockIdx.y, i2_0 = blockIdx.x * TR, i2 = i2_0 + rs;
+    const bool active = i2 < op.n2;
+    C* buf = tile + rs * tile_stride_c<L>();
+    __syncthreads();
+    C x[16];
+    if (active) {
+        const long off = c * ((long)n1 * op.n2) + (long)i2 * n1 + t;
+        C zq[8];
+        if (d.w) {
+            const double sc = *d.inv;
+#pragma unroll
+            for (int e = 0, q = 0; e < 16; e++) {
+                const int idx = F0::index(e);
+                if (idx < n1) {
+                    double2 u = d.w[off + idx];
+                    u.x *= sc;
+                    u.y *= sc;
+                    d.w[off + idx] = u;
+                    zq[q++] = make_float2((float)u.x, (float)u.y);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0, q = 0; e < 16; e++)
+                if (F0::index(e) < n1) zq[q++] = d.x[off + F0::index(e)];
+        }
+        for (int i0 = 0; i0 < d.r; i0 += 4) {
+            C a[4][8];
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const C* p = d.V32 + (long)(i0 + v < d.r ? i0 + v : i0) * d.ld + off;
+#pragma unroll
+                for (int e = 0, q = 0; e < 16; e++)
+                    if (F0::index(e) < n1) a[v][q++] = p[F0::index(e)];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                if (i0 + v < d.r) {
+                    const C cv = cs[i0 + v];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        zq[q].x = fmaf(a[v][q].x, cv.x, zq[q].x);
+                        zq[q].x = fmaf(-a[v][q].y, cv.y, zq[q].x);
+                        zq[q].y = fmaf(a[v][q].x, cv.y, zq[q].y);
+                        zq[q].y = fmaf(a[v][q].y, cv.x, zq[q].y);
+                    }
+                }
+            }
+        }
+        const C* cr = chi + (long)i2 * n1 + t;
+#pragma unroll
+        for (int e = 0, q = 0; e < 16; e++) {
+            const int idx = F0::index(e);
+            if (idx < n1) {
+                zout[off + idx] = zq[q];
+                x[e] = cmul(zq[q], cr[idx]);
+                q++;
+            } else {
+                x[e] = czero<C>();
+            }
         }
         F0::compute(x, t, op.tw1);
         F0::store(buf, x, t);
@@ -418,7 +505,7 @@ __global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_f
         }
     }
     pdl_wait();
-    if (skip && *skip) {
+    if (block_flag(skip)) {
         cp_async_wait_all();
         return;
     }
@@ -508,7 +595,7 @@ __global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T>
         }
     }
     pdl_wait();
-    if (skip && *skip) {
+    if (block_flag(skip)) {
         cp_async_wait_all();
         return;
     }
@@ -573,7 +660,7 @@ __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __rest
     constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2, ns = P2<L>::inv.ns;
     using IL = typename PlanStage<C, L, true, ns - 1>::St;
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -610,7 +697,7 @@ __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict
     using F0 = typename PlanStage<C, L, false, 0>::St;
     static_assert(IL::kR == F0::kR, "the inverse plan is the reversed forward plan");
     pdl_wait();
-    if (skip && *skip) return;
+    if (block_flag(skip)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -675,11 +762,14 @@ inline Launch cols_launch(const OpDev<T>& v, int* stage_g) {
     return Launch{dim3(v.M1), dim3(2 * (v.M2 / v.f2.ept)), *stage_g ? staged : base};
 }
 
-// Launch a kernel instantiation, raising its dynamic shared-memory limit on first use.
+// Launch a kernel instantiation, raising its dynamic shared-memory limit on first use
+// to what the 227 KB per block leaves beside the kernel's static shared memory.
 template <typename K, typename... Args>
 inline void launch_kernel(K kernel, bool& attr_set, const Launch& l, cudaStream_t st, Args... args) {
     if (!attr_set) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncAttributes fa = {};
+        const size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
         attr_set = true;
     }
     launch_pdl(kernel, l.grid, l.block, l.smem, st, args...);

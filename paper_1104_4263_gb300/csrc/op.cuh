@@ -70,6 +70,25 @@ die_status apply_op_skip_xy(dieop_s* op, Contrast c, const IX* x, IY* y, const i
 template <typename T, typename IX, typename IY>
 die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st);
 
+// Input of a product whose first row pass also applies the deflation preconditioner of
+// the FP32-inner solves: z = v + V32 cf, with v = w * (*inv) (the FP64 Arnoldi vector,
+// normalised in place) or, when w is NULL, v = x (complex64).
+struct DeflIn {
+    const float2* V32 = nullptr;   // r vectors, vector i at V32 + i * ld
+    long ld = 0;
+    int r = 0;                     // 1 <= r <= 32
+    const float2* cf = nullptr;    // r coefficients
+    const float2* x = nullptr;
+    double2* w = nullptr;
+    const double* inv = nullptr;
+};
+// y = Atilde z with z = P^-1 v formed inside the first row pass (z is also stored, for
+// the later passes); Atilde = A_R A when reg, else A.  Only for grids on the
+// compile-time FFT path along x1 (defl_product_ok).
+bool defl_product_ok(const dieop_s* op);
+die_status apply_defl_xy(dieop_s* op, const DeflIn& d, float2* z, double2* y, bool reg, const int* skip,
+                         cudaStream_t st);
+
 die_status set_kernel_attributes(const dieop_s* op);
 
 }  // namespace die
