@@ -165,28 +165,40 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ work model per kernel class
+def product_bytes(p, op, s, out_s=None, defl_r=0):
+    """Algorithmic bytes of one regularised product A_R A (five passes K1 K2 K3K1 K2 K3)
+    with element size s: each pass reads its inputs and writes its outputs once; the
+    transposed row spectra W (2 x M1 x n2) go through HBM between passes, the Green
+    spectra are the quarter planes (3 x Q1 x Q2).  defl_r > 0: the first row pass also
+    applies the deflation (reads r complex64 basis vectors and the FP64 Arnoldi vector,
+    writes it back normalised and stores z)."""
+    N, n = p.N, 2 * p.N
+    out_s = out_s or s
+    Wb = 2 * op.M1 * p.n2 * s
+    Q = (op.M1 // 2 + 1) * (op.M2 // 2 + 1)
+    k1 = n * s + N * s + Wb
+    if defl_r:
+        k1 = defl_r * n * 8 + 2 * n * 16 + n * 8 + N * s + Wb
+    k2 = 2 * Wb + 3 * Q * s
+    k3k1 = Wb + n * s + N * s + n * s + Wb
+    k3 = Wb + n * s + n * out_s
+    return {"rows_fwd": k1, "cols_green": 2 * k2, "rows_inv_fwd": k3k1, "rows_inv": k3}
+
+
 def work_model(cls, p, op, r, steps_per_cycle, cycles, products, fp64_products):
     """Algorithmic work of all launches of a kernel class in the timed region:
-    ('hbm', bytes) or ('alu', FP64 flops).  Products: complex64 ones inside the cycles,
-    FP64 ones for the restart residuals; both counted at their own element sizes."""
-    N, n2, M1 = p.N, p.n2, op.M1
-    Wb = lambda s: 2 * M1 * n2 * s                      # transposed row spectra
-    Q = (op.M1 // 2 + 1) * (op.M2 // 2 + 1)
-    n = 2 * N
-    if cls == "cols_green":
-        per = lambda s: 2 * Wb(s) + 3 * Q * s
-        return "hbm", 2 * products * per(8) + 2 * fp64_products * per(16)
-    if cls == "rows_fwd":
-        return "hbm", products * (n * 8 + N * 8 + Wb(8)) + fp64_products * (n * 16 + N * 16 + Wb(16))
-    if cls == "rows_inv_fwd":
-        return "hbm", (products * (Wb(8) + n * 8 + N * 8 + n * 8 + Wb(8))
-                       + fp64_products * (Wb(16) + n * 16 + N * 16 + n * 16 + Wb(16)))
-    if cls == "rows_inv":
-        return "hbm", products * (Wb(8) + n * 8 + n * 16) + fp64_products * (Wb(16) + 2 * n * 16)
-    if cls == "dots32":
-        return "hbm", products * (r * n * 8 + n * 8)
-    if cls == "defl_update":
-        return "hbm", products * (r * n * 8 + 2 * n * 8)
+    ('hbm', bytes) or ('alu', FP64 flops).  Products: the deflated complex64 ones inside
+    the cycles (complex128 output), and the FP64 restart residuals; each counted at its
+    own element size."""
+    n = 2 * p.N
+    if cls in ("rows_fwd", "cols_green", "rows_inv_fwd", "rows_inv"):
+        c64 = product_bytes(p, op, 8, out_s=16, defl_r=r)[cls]
+        c128 = product_bytes(p, op, 16)[cls]
+        return "hbm", products * c64 + fp64_products * c128
+    if cls == "dots32":                     # cf of v_0, once per cycle
+        return "hbm", cycles * (r * n * 8 + n * 8)
+    if cls == "defl_update":                # FP64 P^-1 in the update of x, once per cycle
+        return "hbm", cycles * (r * n * 16 + 2 * n * 16)
     m = steps_per_cycle
     if cls == "dots":
         # step j of a cycle: j+1 projections + the norm of w; per cycle one norm of the
@@ -415,9 +427,20 @@ def matvec_rates(op, p, die, torch):
             e1.record(s)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
+        s_el = 8 if name == "c64" else 16
+        nbytes = sum(product_bytes(p, o, s_el).values())
+        gbs = nbytes / (ms / reps / 1e3) / 1e9
         out[name] = {"regularized_per_s": reps / (ms / 1e3), "us_per_product": 1e3 * ms / reps,
+                     "algorithmic_bytes": nbytes, "GBps": gbs, "hbm_frac": gbs / hbm_peak(),
                      "l2": "flushed (256 MB write) before each product"}
     return out
+
+
+def hbm_peak():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError):
+        return 6800.0
 
 
 def plain_fp64(op, b, step_iters, step_s, last):
