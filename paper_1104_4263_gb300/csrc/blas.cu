@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(kRedThreads, 2) proj32_kernel(const float2* __
 __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2* __restrict__ V, long ldv, int r,
                                                                     const float2* __restrict__ cf,
                                                                     const float2* x, float2* z, long n,
-                                                                    const int* skip, double2* w, const double* inv) {
+                                                                    const int* skip, double2* w, const double* inv,
+                                                                    double* wm) {
     pdl_wait();
     if (block_flag(skip)) return;
     __shared__ float2 cs[kMaxBasis];
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(kRedThreads) defl_update32_kernel(const float2
             u.x *= sc;
             u.y *= sc;
             w[idx] = u;
+            if (wm) wm[idx] = u.x - u.y;
             acc = make_float2((float)u.x, (float)u.y);
         } else {
             acc = x[idx];
@@ -333,13 +335,14 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
                                                                  const double2* __restrict__ s, const double2* base,
                                                                  double2* out, long n, double2* nrm2, Dgks dec,
                                                                  int has_dec, RedScratch rs, const int* skip,
-                                                                 int live) {
+                                                                 int live, const double* VM) {
     using A = typename acc_of<VT>::type;
     pdl_wait();
     const bool off = block_flag(skip);
     if (off && !(NORM && live)) return;
     __shared__ VT cs[kMaxBasis];
     __shared__ A csn[kMaxBasis];            // -Im(c): every step below is a plain FMA
+    __shared__ double c3[3][kMaxBasis];     // VM != NULL: Im c, Re c - Im c, Re c + Im c
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         double cx = 0, cy = 0;
         if (M) {
@@ -357,6 +360,9 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
         c.y = (A)cy;
         cs[i] = c;
         csn[i] = -c.y;
+        c3[0][i] = cy;
+        c3[1][i] = cx - cy;
+        c3[2][i] = cx + cy;
     }
     __syncthreads();
     double nacc = 0;
@@ -365,11 +371,25 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nn; idx += stride) {
         A x0 = 0, y0 = 0;
         if (base) { const double2 bv = base[idx]; x0 = (A)bv.x; y0 = (A)bv.y; }
+        if (VM) {   // three-multiplication form: c a = (K1 + K2) + i (K1 + K3)
+            double k1 = 0, k2 = 0, k3 = 0;
 #pragma unroll 4
-        for (int i = 0; i < k; i++) {
-            const VT a = V[(long)i * ldv + idx], c = cs[i];
-            x0 = fmac(a.x, c.x, x0); x0 = fmac(a.y, csn[i], x0);
-            y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
+            for (int i = 0; i < k; i++) {
+                const VT a = V[(long)i * ldv + idx];
+                const double m = VM[(long)i * ldv + idx];
+                k1 = fma(c3[0][i], m, k1);
+                k2 = fma(c3[1][i], (double)a.x, k2);
+                k3 = fma(c3[2][i], (double)a.y, k3);
+            }
+            x0 += (A)(k1 + k2);
+            y0 += (A)(k1 + k3);
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < k; i++) {
+                const VT a = V[(long)i * ldv + idx], c = cs[i];
+                x0 = fmac(a.x, c.x, x0); x0 = fmac(a.y, csn[i], x0);
+                y0 = fmac(a.x, c.y, y0); y0 = fmac(a.y, c.x, y0);
+            }
         }
         const double2 o = make_double2((double)x0, (double)y0);
         out[idx] = o;
@@ -405,16 +425,20 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
                                                                       const double2* base, double2* out, long n,
                                                                       double2* nrm2, Dgks dec, int has_dec,
                                                                       DeflProj dp, RedScratch rs, const int* skip,
-                                                                      int live) {
+                                                                      int live, const double* VM) {
     pdl_wait();
     const bool off = block_flag(skip);
     if (off && !live) return;
     __shared__ double2 cs[kMaxBasis];
     __shared__ double csn[kMaxBasis];
+    __shared__ double c3[3][kMaxBasis];     // VM != NULL: Im c, Re c - Im c, Re c + Im c
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double2 c = make_double2(-coef[i].x, -coef[i].y);
         cs[i] = c;
         csn[i] = -c.y;
+        c3[0][i] = c.y;
+        c3[1][i] = c.x - c.y;
+        c3[2][i] = c.x + c.y;
     }
     __syncthreads();
     double nacc = 0;
@@ -428,11 +452,25 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nn; idx += stride) {
         double x0 = 0, y0 = 0;
         if (base) { const double2 bv = base[idx]; x0 = bv.x; y0 = bv.y; }
+        if (VM) {   // three-multiplication form: c a = (K1 + K2) + i (K1 + K3)
+            double k1 = 0, k2 = 0, k3 = 0;
 #pragma unroll 4
-        for (int i = 0; i < k; i++) {
-            const double2 a = V[(long)i * ldv + idx], c = cs[i];
-            x0 = fma(a.x, c.x, x0); x0 = fma(a.y, csn[i], x0);
-            y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+            for (int i = 0; i < k; i++) {
+                const double2 a = V[(long)i * ldv + idx];
+                const double m = VM[(long)i * ldv + idx];
+                k1 = fma(c3[0][i], m, k1);
+                k2 = fma(c3[1][i], a.x, k2);
+                k3 = fma(c3[2][i], a.y, k3);
+            }
+            x0 += k1 + k2;
+            y0 += k1 + k3;
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < k; i++) {
+                const double2 a = V[(long)i * ldv + idx], c = cs[i];
+                x0 = fma(a.x, c.x, x0); x0 = fma(a.y, csn[i], x0);
+                y0 = fma(a.x, c.y, y0); y0 = fma(a.y, c.x, y0);
+            }
         }
         const double2 o = make_double2(x0, y0);
         out[idx] = o;
@@ -558,29 +596,31 @@ __global__ void arnoldi_finish_kernel(GmresDev S, int j, int step) {
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hgl[i] = col[i];
 }
 
-// v *= inv, with an optional complex64 copy of the result
-__device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float2* v32) {
+// v *= inv, with an optional complex64 copy of the result and its Re - Im (vm)
+__device__ __forceinline__ void scale_rows(double2* v, long n, double inv, float2* v32, double* vm) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const double2 a = v[i];
         const double2 b = make_double2(a.x * inv, a.y * inv);
         v[i] = b;
         if (v32) v32[i] = make_float2((float)b.x, (float)b.y);
+        if (vm) vm[i] = b.x - b.y;
     }
 }
 
-__global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32) {
+__global__ void scale_inv_sqrt_kernel(double2* v, long n, const double2* nrm2, const int* skip, float2* v32,
+                                      double* vm) {
     pdl_wait();
     if (block_flag(skip)) return;
     __shared__ double s_inv;
     if (threadIdx.x == 0) s_inv = inv_norm(nrm2->x);
     __syncthreads();
-    scale_rows(v, n, s_inv, v32);
+    scale_rows(v, n, s_inv, v32, vm);
 }
 
-__global__ void scale_by_kernel(double2* v, long n, const double* inv, const int* skip, float2* v32) {
+__global__ void scale_by_kernel(double2* v, long n, const double* inv, const int* skip, float2* v32, double* vm) {
     pdl_wait();
     if (block_flag(skip)) return;
-    scale_rows(v, n, *inv, v32);
+    scale_rows(v, n, *inv, v32, vm);
 }
 
 __global__ void sub_kernel(const double2* b, const double2* y, double2* r, long n) {
@@ -652,16 +692,16 @@ die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, co
 }
 die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
                         double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs, const int* skip,
-                        cudaStream_t st, bool live) {
+                        cudaStream_t st, bool live, const double* VM) {
     if (k > kMaxBasis || k < 0) return DIE_EINVAL;
     const Dgks d = dec ? *dec : Dgks{};
     const int has_dec = dec && dec->reorth ? 1 : 0;
     if (nrm2) {
         DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(basis_axpy_kernel<double2, true>, dim3(kRedBlocks), dim3(kRedThreads), 0, st,
-                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0));
+                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0, VM));
     } else {
         DIE_PROF(PK_LINCOMB, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
-                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, (double2*)nullptr, d, 0, rs, skip, 0));
+                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, (double2*)nullptr, d, 0, rs, skip, 0, (const double*)nullptr));
     }
     DIE_LAUNCH_CHECK();
     return DIE_OK;
@@ -670,14 +710,14 @@ die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, co
                          double2* z, long n, const int* skip, cudaStream_t st) {
     if (r > kMaxBasis || r < 1) return DIE_EINVAL;
     DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
-                 V, ldv, r, (const double2*)nullptr, 1.0, M, s, x, z, n, (double2*)nullptr, Dgks{}, 0, RedScratch{}, skip, 0));
+                 V, ldv, r, (const double2*)nullptr, 1.0, M, s, x, z, n, (double2*)nullptr, Dgks{}, 0, RedScratch{}, skip, 0, (const double*)nullptr));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
 die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
-                           const int* skip, cudaStream_t st, double2* w, const double* inv) {
+                           const int* skip, cudaStream_t st, double2* w, const double* inv, double* wm) {
     if (r > kMaxBasis || r < 1 || (inv && !w)) return DIE_EINVAL;
-    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(defl_update32_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, V, ldv, r, cf, x, z, n, skip, w, inv));
+    DIE_PROF(PK_DEFL_UPDATE, st, launch_pdl(defl_update32_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, V, ldv, r, cf, x, z, n, skip, w, inv, wm));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -685,11 +725,11 @@ die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, c
 // Update pass with the deflation projections folded in (see cgs_update_defl_kernel).
 static die_status k_update_defl(const double2* V, long ldv, int k, const double2* coef, double2* w, long n,
                                 double2* nrm2, const Dgks& dec, int has_dec, const DeflProj& dp, const RedScratch& rs,
-                                const int* skip, cudaStream_t st, bool live) {
+                                const int* skip, cudaStream_t st, bool live, const double* VM) {
     if (k > kMaxBasis || k < 0 || dp.r < 1 || dp.r > kDeflFoldMax) return DIE_EINVAL;
     const int ng = (dp.r + 7) / 8;
 #define UPD_CASE(NG) DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(cgs_update_defl_kernel<NG>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, \
-                              V, ldv, k, coef, (const double2*)w, w, n, nrm2, dec, has_dec, dp, rs, skip, live ? 1 : 0))
+                              V, ldv, k, coef, (const double2*)w, w, n, nrm2, dec, has_dec, dp, rs, skip, live ? 1 : 0, VM))
     switch (ng) {
         case 1: UPD_CASE(1); break;
         case 2: UPD_CASE(2); break;
@@ -703,7 +743,7 @@ static die_status k_update_defl(const double2* V, long ldv, int k, const double2
 
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
                     int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st,
-                    double* inv, const DeflProj* dp) {
+                    double* inv, const DeflProj* dp, double* VM) {
     Dgks dec;
     dec.before2 = h1 + nv;
     dec.reorth = reorth;
@@ -713,28 +753,30 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.always = eta2 >= 1.0 ? 1 : 0;
     dec.eta2 = eta2;
     DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true));
-    if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true));
-    else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true));
+    if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true, VM));
+    else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true, VM));
     Dgks last;                       // second pass: no decision, only the scale factor
     last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;
     die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st);
     g_prof_override = PK_UPDATE_REORTH;
     if (s == DIE_OK) {
-        s = dp ? k_update_defl(V, ldv, nv, h2, w, n, nrm + 1, last, 0, *dp, rs, skip2, st, false)
-               : k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st);
+        s = dp ? k_update_defl(V, ldv, nv, h2, w, n, nrm + 1, last, 0, *dp, rs, skip2, st, false, VM)
+               : k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st, false, VM);
     }
     g_prof_override = -1;
     return s;
 }
 
-die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32) {
-    DIE_PROF(PK_SCALE, st, launch_pdl(scale_inv_sqrt_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, nrm2, skip, v32));
+die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32,
+                            double* vm) {
+    DIE_PROF(PK_SCALE, st, launch_pdl(scale_inv_sqrt_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, nrm2, skip, v32, vm));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st, float2* v32) {
-    DIE_PROF(PK_SCALE, st, launch_pdl(scale_by_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, inv, skip, v32));
+die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st, float2* v32,
+                      double* vm) {
+    DIE_PROF(PK_SCALE, st, launch_pdl(scale_by_kernel, dim3(grid_for(n)), dim3(kRedThreads), 0, st, v, n, inv, skip, v32, vm));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

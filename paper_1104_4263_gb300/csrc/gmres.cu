@@ -55,7 +55,7 @@ SolverCache* solver_cache(dieop_s* op) { return reinterpret_cast<SolverCache*>(o
 void free_solver_cache(dieop_s* op) {
     SolverCache* c = solver_cache(op);
     if (!c) return;
-    void* ptrs[] = {c->V, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->one};
+    void* ptrs[] = {c->V, c->Vm, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->one};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_red_scratch(&c->rs);
@@ -88,7 +88,8 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     c->n = n;
     c->hist_cap = hist_cap;
     auto al = [](void** p, size_t b) { return cudaMalloc(p, b) == cudaSuccess; };
-    bool ok = al((void**)&c->V, (size_t)(m + 1) * n * sizeof(double2)) && al((void**)&c->btil, n * sizeof(double2)) &&
+    bool ok = al((void**)&c->V, (size_t)(m + 1) * n * sizeof(double2)) &&
+              al((void**)&c->Vm, (size_t)(m + 1) * n * sizeof(double)) && al((void**)&c->btil, n * sizeof(double2)) &&
               al((void**)&c->tmp, n * sizeof(double2)) && al((void**)&c->z, n * sizeof(double2)) &&
               al((void**)&c->v32, n * sizeof(float2)) && al((void**)&c->z32, n * sizeof(float2)) &&
               al((void**)&c->small, small_count(m) * sizeof(double2)) &&
@@ -296,6 +297,10 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     // update of step j+1 normalises v_{j+1}; otherwise they run as their own pass.
     const bool fold = defl32 && defl->r <= kDeflFoldMax;
     const bool fold_product = fold && defl_product_ok(op);   // deflation inside the first row pass
+    // Update passes in the three-multiplication form: every kernel that normalises a basis
+    // vector also stores its Re - Im in c->Vm (all paths but the separate complex64
+    // projection pass of r > kDeflFoldMax).
+    double* Vm = (defl32 && !fold) ? nullptr : c->Vm;
     DeflProj dp;
     if (fold) {
         dp.V32 = defl->V32;
@@ -326,7 +331,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (!isfinite(rel)) { status = DIE_ENAN; break; }
         if (rel <= o->tol) { status = DIE_OK; break; }
         if (iters >= o->max_iters) break;
-        DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32));
+        DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32, Vm));
         if (fold)   // cf for v_0
             DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, defl->s, defl->M32, defl->c32,
                              defl->rs, nullptr, st));
@@ -351,11 +356,12 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
                 din.x = c->v32;
                 din.w = j > 0 ? vj : nullptr;
                 din.inv = inv_prev;
+                din.wm = j > 0 && Vm ? Vm + (long)j * ldv : nullptr;
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
                 DIE_TRY(apply_defl_xy(op, din, c->z32, w, reg, S.done, st));
             } else if (fold) {
                 DIE_TRY(k_defl_update32(defl->V32, n, defl->r, defl->c32, c->v32, c->z32, n, S.done, st,
-                                        j > 0 ? vj : nullptr, inv_prev));
+                                        j > 0 ? vj : nullptr, inv_prev, j > 0 && Vm ? Vm + (long)j * ldv : nullptr));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
                 DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
                             : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
@@ -365,7 +371,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
                 DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
                             : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
             } else {
-                if (inv_prev) DIE_TRY(k_scale_by(vj, n, inv_prev, S.done, st));
+                if (inv_prev) DIE_TRY(k_scale_by(vj, n, inv_prev, S.done, st, nullptr, Vm ? Vm + (long)j * ldv : nullptr));
                 const double2* src = vj;
                 if (defl) {
                     DIE_TRY(defl_apply(defl, vj, c->z, S.done, st, true));
@@ -376,7 +382,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
             }
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
             DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1 + (long)j * (m + 3), S.h2 + (long)j * (m + 3), S.nrm + 2 * j,
-                             S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j, fold ? &dp : nullptr));
+                             S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j, fold ? &dp : nullptr,
+                             Vm));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
             DIE_CUDA_TRY(cudaEventRecord(c->fork, st));
             DIE_CUDA_TRY(cudaStreamWaitEvent(side, c->fork, 0));

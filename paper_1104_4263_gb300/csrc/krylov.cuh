@@ -102,7 +102,7 @@ die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, co
 // nrm2 != NULL: ||out||^2 into nrm2[0] (device), and the DGKS decision if dec != NULL.
 die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
                         double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs,
-                        const int* skip, cudaStream_t st, bool live = false);
+                        const int* skip, cudaStream_t st, bool live = false, const double* VM = nullptr);
 // z = x + V (M s); M r x r column-major; s the projections V^* x.  z may equal x.
 die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, const double2* s, const double2* x,
                          double2* z, long n, const int* skip, cudaStream_t st);
@@ -110,7 +110,8 @@ die_status k_defl_update(const double2* V, long ldv, int r, const double2* M, co
 // from a folded update.  With inv != NULL the input is formed from the FP64 vector w:
 // w *= *inv (written back) and x = complex64(w) (x itself is then not read).
 die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, const float2* x, float2* z, long n,
-                           const int* skip, cudaStream_t st, double2* w = nullptr, const double* inv = nullptr);
+                           const int* skip, cudaStream_t st, double2* w = nullptr, const double* inv = nullptr,
+                           double* wm = nullptr);
 
 // Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion (done is a
 // live flag, see above):
@@ -118,16 +119,19 @@ die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, c
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
 // inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).
 // dp != NULL folds the deflation projections of the final w into the update passes.
+// VM != NULL: the update passes in the three-multiplication form, with m = Re - Im of each
+// basis vector V_i stored in VM (same stride as V) by whatever normalised V_i.
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2,
                     double2* nrm, int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs,
-                    cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr);
+                    cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr, double* VM = nullptr);
 
 // v *= 1 / sqrt(re(*nrm2)) if positive; v *= *inv.  v32 != NULL also receives the
 // scaled vector rounded to complex64.
+// vm != NULL also receives Re - Im of the scaled vector (three-multiplication form).
 die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st,
-                            float2* v32 = nullptr);
+                            float2* v32 = nullptr, double* vm = nullptr);
 die_status k_scale_by(double2* v, long n, const double* inv, const int* skip, cudaStream_t st,
-                      float2* v32 = nullptr);
+                      float2* v32 = nullptr, double* vm = nullptr);
 // r = b - y
 die_status k_sub(const double2* b, const double2* y, double2* r, long n, cudaStream_t st);
 // complex128 -> complex64 copy

@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, c
                     u.x *= sc;
                     u.y *= sc;
                     d.w[off + idx] = u;
+                    if (d.wm) d.wm[off + idx] = u.x - u.y;
                     zq[q++] = make_float2((float)u.x, (float)u.y);
                 }
             }

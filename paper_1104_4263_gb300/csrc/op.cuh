@@ -81,6 +81,7 @@ struct DeflIn {
     const float2* x = nullptr;
     double2* w = nullptr;
     const double* inv = nullptr;
+    double* wm = nullptr;          // may be NULL: receives Re - Im of the normalised w
 };
 // y = Atilde z with z = P^-1 v formed inside the first row pass (z is also stored, for
 // the later passes); Atilde = A_R A when reg, else A.  Only for grids on the

@@ -14,6 +14,7 @@ struct SolverCache {
     long n = 0;             // vector length 2N
     int hist_cap = 0;
     double2* V = nullptr;   // (m_cap + 1) * n
+    double* Vm = nullptr;   // (m_cap + 1) * n: Re - Im of each basis vector (three-multiplication form)
     double2* btil = nullptr;
     double2* tmp = nullptr;
     double2* z = nullptr;
