@@ -209,6 +209,77 @@ __device__ __forceinline__ void proj_group(const VT* __restrict__ V, long ldv, i
     block_partials<A, K, CNT>(acc, red, g0, rs);
 }
 
+// Three-multiplication (Gauss) form of the FP64 projections.  With m = a.x - a.y stored
+// beside each basis vector (VM, same stride as V):
+//   conj(a) b = (P1 - P2) + i (P2 - P3),  P1 = a.x (b.x + b.y),  P2 = m b.y,  P3 = a.y (b.x - b.y),
+// three FMAs per term instead of four; the two sums of b are formed once per row.  The
+// vector itself (index nv, the norm) takes m = b.x - b.y.
+template <int CNT>
+__device__ __forceinline__ void proj_group3(const double2* __restrict__ V, const double* __restrict__ VM, long ldv,
+                                            int g0, int nv, const double2* __restrict__ w, long n, double* red,
+                                            const RedScratch& rs) {
+    constexpr int K = pow2ceil<2 * CNT>();
+    double p1[CNT], p2[CNT], p3[CNT];
+#pragma unroll
+    for (int v = 0; v < CNT; v++) { p1[v] = 0; p2[v] = 0; p3[v] = 0; }
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const double2 b = w[idx];
+        double2 a[CNT];
+        double m[CNT];
+#pragma unroll
+        for (int v = 0; v < CNT; v++) {
+            const int i = g0 + v;
+            a[v] = i < nv ? V[(long)i * ldv + idx] : b;
+            m[v] = i < nv ? VM[(long)i * ldv + idx] : b.x - b.y;
+        }
+        const double sb = b.x + b.y, db = b.x - b.y;
+#pragma unroll
+        for (int v = 0; v < CNT; v++) {
+            p1[v] = fma(a[v].x, sb, p1[v]);
+            p2[v] = fma(m[v], b.y, p2[v]);
+            p3[v] = fma(a[v].y, db, p3[v]);
+        }
+    }
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = 0;
+#pragma unroll
+    for (int v = 0; v < CNT; v++) {
+        acc[2 * v] = p1[v] - p2[v];
+        acc[2 * v + 1] = p2[v] - p3[v];
+    }
+    block_partials<double, K, CNT>(acc, red, g0, rs);
+}
+
+template <int C>
+__device__ __forceinline__ void proj_group3_n(int cnt, const double2* V, const double* VM, long ldv, int g0, int nv,
+                                              const double2* w, long n, double* red, const RedScratch& rs) {
+    if (cnt == C) proj_group3<C>(V, VM, ldv, g0, nv, w, n, red, rs);
+    else if constexpr (C > 1) proj_group3_n<C - 1>(cnt, V, VM, ldv, g0, nv, w, n, red, rs);
+}
+
+// FP64 projections in the three-multiplication form, kGroup3 vectors per pass.
+constexpr int kGroup3 = 6;
+__global__ void __launch_bounds__(kRedThreads, 2) proj3_kernel(const double2* __restrict__ V,
+                                                               const double* __restrict__ VM, long ldv, int nv,
+                                                               const double2* __restrict__ w, long n, int with_norm,
+                                                               double2* out, RedScratch rs, const int* skip,
+                                                               int live) {
+    constexpr int K = pow2ceil<2 * kGroup3>();
+    __shared__ double red[(kRedThreads / 32) * K];
+    pdl_wait();
+    const bool off = block_flag(skip);
+    if (off && !live) return;
+    const int nvt = nv + (with_norm ? 1 : 0);
+    for (int g0 = 0; g0 < nvt; g0 += kGroup3) {
+        if (off) { zero_partials(g0, 2 * kGroup3, nvt, rs); continue; }
+        const int cnt = nvt - g0 < kGroup3 ? nvt - g0 : kGroup3;
+        proj_group3_n<kGroup3>(cnt, V, VM, ldv, g0, nv, w, n, red, rs);
+    }
+    reduce_partials(rs, nvt, out);
+}
+
 // Runtime count -> compile-time CNT in [1, C].
 template <typename VT, int C, bool SCALE>
 __device__ __forceinline__ void proj_group_n(int cnt, const VT* V, long ldv, int g0, int nv, const VT* xin, VT* xout,
@@ -676,9 +747,12 @@ static inline int grid_for(long n) {
 constexpr int kGroupFp64 = 8;        // FP64 projections per group (16 running sums per thread)
 
 die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
-                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live) {
+                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live, const double* VM) {
     if (nv + 1 > kMaxBasis || nv < 0) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS, st, launch_pdl(proj_kernel<double2, kGroupFp64>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
+    if (VM)
+        DIE_PROF(PK_DOTS, st, launch_pdl(proj3_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, VM, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
+    else
+        DIE_PROF(PK_DOTS, st, launch_pdl(proj_kernel<double2, kGroupFp64>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -752,13 +826,13 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.inv = inv;
     dec.always = eta2 >= 1.0 ? 1 : 0;
     dec.eta2 = eta2;
-    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true));
+    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true, VM));
     if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true, VM));
     else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true, VM));
     Dgks last;                       // second pass: no decision, only the scale factor
     last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;
-    die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st);
+    die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st, false, VM);
     g_prof_override = PK_UPDATE_REORTH;
     if (s == DIE_OK) {
         s = dp ? k_update_defl(V, ldv, nv, h2, w, n, nrm + 1, last, 0, *dp, rs, skip2, st, false, VM)

@@ -89,8 +89,10 @@ struct GmresDev {
 // still take part in the final sums, so that the arrival counters stay consistent.
 //
 // out[i] = V_i^* w for i < nv; with_norm: out[nv] = ||w||^2 (real part).
+// VM != NULL: the three-multiplication form, with m = Re - Im of every V_i in VM.
 die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm, double2* out,
-                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live = false);
+                  const RedScratch& rs, const int* skip, cudaStream_t st, bool live = false,
+                  const double* VM = nullptr);
 // Deflation projections of the FP32-inner solves: s = V^* x with a complex64 basis and
 // vector (FP32 products and in-block sums, FP64 across blocks), then cf = M s rounded to
 // complex64 (M32: the r x r matrix M in complex64, column-major).  With inv != NULL, x
@@ -119,8 +121,8 @@ die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, c
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
 // inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).
 // dp != NULL folds the deflation projections of the final w into the update passes.
-// VM != NULL: the update passes in the three-multiplication form, with m = Re - Im of each
-// basis vector V_i stored in VM (same stride as V) by whatever normalised V_i.
+// VM != NULL: both passes in the three-multiplication form, with m = Re - Im of each basis
+// vector V_i stored in VM (same stride as V) by whatever normalised V_i.
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2,
                     double2* nrm, int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs,
                     cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr, double* VM = nullptr);
