@@ -427,6 +427,26 @@ def matvec_rates(op, p, die, torch):
             e1.record(s)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
+        if name == "c64":   # the same products batched over 8 right-hand sides (e.g. incidence angles)
+            nb = 8
+            xb = torch.randn(nb, 2, p.n2, p.n1, dtype=dt, device="cuda")
+            yb = torch.empty_like(xb)
+            for _ in range(3):
+                o.apply_batch(xb, yb, regularized=True)
+            msb = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                o.apply_batch(xb, yb, regularized=True)
+                e1.record(s)
+                torch.cuda.synchronize()
+                msb += e0.elapsed_time(e1)
+            nbytes_b = nb * sum(product_bytes(p, o, 8).values())
+            out["c64_batch8"] = {"regularized_per_s": nb * reps / (msb / 1e3), "us_per_product": 1e3 * msb / reps / nb,
+                                 "GBps": nbytes_b / (msb / reps / 1e3) / 1e9,
+                                 "hbm_frac": nbytes_b / (msb / reps / 1e3) / 1e9 / hbm_peak(),
+                                 "note": "8 right-hand sides per call (dieop_apply_batch), L2 flushed before each call"}
         s_el = 8 if name == "c64" else 16
         nbytes = sum(product_bytes(p, o, s_el).values())
         gbs = nbytes / (ms / reps / 1e3) / 1e9

@@ -96,6 +96,18 @@ die_status dieop_apply_regularized(dieop_t op, const void* x, void* y, void* str
 /* y = A(chi') x alone (the regulariser; used for the right-hand side A_R b). */
 die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* stream);
 
+/* Batched products with one operator (many incidence angles of one scatterer):
+ * y_k = A x_k (regularized == 0) or y_k = A(chi') A(chi) x_k (regularized != 0), k < nrhs.
+ * x, y: device, nrhs field vectors one after another (vector k starts at element
+ * k * 2 n1 n2), each laid out as for dieop_apply, complex128 (prec DIE_FP64) or complex64
+ * (DIE_FP32_INNER); y may equal x.  Every pass of the product runs as one launch over all
+ * right-hand sides, so the kernels see nrhs times more independent work per launch.  The
+ * operator keeps a workspace of nrhs sets of row spectra (2 M1 n2) and middle vectors
+ * (2 n1 n2), grown on the first call with a larger nrhs (that call synchronises the
+ * device).  Results are identical to nrhs separate calls.  DIE_EINVAL: NULL pointer or
+ * nrhs outside [1, 1024]; DIE_ENOMEM: the workspace does not fit. */
+die_status dieop_apply_batch(dieop_t op, int nrhs, const void* x, void* y, int regularized, void* stream);
+
 /* b = incident TE plane wave of unit |E| at angle psi to the x1 axis (Section 4, end):
  * H3 = exp(i k_b (x1 cos psi + x2 sin psi)), E1 = -sin(psi) H3, E2 = cos(psi) H3.
  * b: device, 2*n1*n2 complex128.  Errors: DIE_EINVAL, DIE_ECUDA. */

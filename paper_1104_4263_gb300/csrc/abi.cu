@@ -91,7 +91,7 @@ using namespace die;
 static void free_op(dieop_s* op) {
     if (!op) return;
     void* ptrs[] = {op->tw1_d, op->tw2_d, op->tw1_f, op->tw2_f, op->gq_d, op->gq_f, op->chi_d, op->chir_d,
-                    op->chi_f, op->chir_f, op->ws.W, op->ws.v, op->dflag};
+                    op->chi_f, op->chir_f, op->ws.W, op->ws.v, op->wsb.W, op->wsb.v, op->dflag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_solver_cache(op);
@@ -238,6 +238,32 @@ static die_status apply_any(dieop_t op, const void* x, void* y, void* stream, in
 }
 
 die_status dieop_apply(dieop_t op, const void* x, void* y, void* stream) { return apply_any(op, x, y, stream, 0); }
+
+die_status dieop_apply_batch(dieop_t op, int nrhs, const void* x, void* y, int regularized, void* stream) {
+    if (!op || !x || !y || nrhs < 1 || nrhs > 1024) return DIE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nrhs > op->wsb_cap) {   // grow the batch workspace (cudaFree waits for work that may use it)
+        if (op->wsb.W) cudaFree(op->wsb.W);
+        if (op->wsb.v) cudaFree(op->wsb.v);
+        op->wsb = Workspace{};
+        op->wsb_cap = 0;
+        const size_t es = op->prec == DIE_FP64 ? sizeof(double2) : sizeof(float2);
+        op->wsb.W_bytes = (size_t)nrhs * 2 * op->M1 * op->n2 * es;
+        op->wsb.v_bytes = (size_t)nrhs * 2 * op->N * es;
+        if (cudaMalloc(&op->wsb.W, op->wsb.W_bytes) != cudaSuccess ||
+            cudaMalloc(&op->wsb.v, op->wsb.v_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (op->wsb.W) cudaFree(op->wsb.W);
+            op->wsb = Workspace{};
+            return DIE_ENOMEM;
+        }
+        op->wsb_cap = nrhs;
+    }
+    const bool reg = regularized != 0;
+    if (op->prec == DIE_FP64)
+        return apply_batch<double, double2>(op, reg, (const double2*)x, (double2*)y, nrhs, op->wsb.W, op->wsb.v, st);
+    return apply_batch<float, float2>(op, reg, (const float2*)x, (float2*)y, nrhs, op->wsb.W, op->wsb.v, st);
+}
 die_status dieop_apply_regularized(dieop_t op, const void* x, void* y, void* stream) {
     return apply_any(op, x, y, stream, 1);
 }

@@ -8,6 +8,8 @@ OpDev<double> view_d(const dieop_s* op) {
     v.n1 = op->n1; v.n2 = op->n2; v.M1 = op->M1; v.M2 = op->M2; v.Q1 = op->Q1; v.Q2 = op->Q2;
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_d; v.tw2 = op->tw2_d; v.gq = op->gq_d;
+    v.xs = 2L * op->n1 * op->n2;
+    v.ws = 2L * op->M1 * op->n2;
     return v;
 }
 OpDev<float> view_f(const dieop_s* op) {
@@ -15,6 +17,8 @@ OpDev<float> view_f(const dieop_s* op) {
     v.n1 = op->n1; v.n2 = op->n2; v.M1 = op->M1; v.M2 = op->M2; v.Q1 = op->Q1; v.Q2 = op->Q2;
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_f; v.tw2 = op->tw2_f; v.gq = op->gq_f;
+    v.xs = 2L * op->n1 * op->n2;
+    v.ws = 2L * op->M1 * op->n2;
     return v;
 }
 
@@ -25,5 +29,7 @@ template die_status apply_op<double, double2>(dieop_s*, Contrast, const double2*
 template die_status apply_reg<double, double2>(dieop_s*, const double2*, double2*, cudaStream_t);
 template die_status apply_op_skip<double, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t);
 template die_status apply_reg_skip<double, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t);
+template die_status apply_batch<double, double2>(dieop_s*, bool, const double2*, double2*, int, void*, void*,
+                                                 cudaStream_t);
 
 }  // namespace die

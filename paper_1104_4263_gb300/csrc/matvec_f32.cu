@@ -9,6 +9,7 @@ template die_status apply_op<float, float2>(dieop_s*, Contrast, const float2*, f
 template die_status apply_op<float, double2>(dieop_s*, Contrast, const double2*, double2*, cudaStream_t);
 template die_status apply_reg<float, float2>(dieop_s*, const float2*, float2*, cudaStream_t);
 template die_status apply_reg<float, double2>(dieop_s*, const double2*, double2*, cudaStream_t);
+template die_status apply_batch<float, float2>(dieop_s*, bool, const float2*, float2*, int, void*, void*, cudaStream_t);
 template die_status apply_op_skip<float, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t);
 template die_status apply_reg_skip<float, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t);
 template die_status apply_op_skip_xy<float, float2, double2>(dieop_s*, Contrast, const float2*, double2*, const int*,

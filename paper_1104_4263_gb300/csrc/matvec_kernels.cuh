@@ -51,6 +51,8 @@ __global__ void __launch_bounds__(512) k1_rows_fwd(OpDev<T> op, const IO* __rest
     using C = C_t<T>;
     pdl_wait();
     if (block_flag(skip)) return;
+    u += blockIdx.z * op.xs;            // right-hand side of a batched product
+    W += blockIdx.z * op.ws;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false);
     const FftPlan pl = LS ? kf : op.f1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -102,6 +104,7 @@ __global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__
     using C = C_t<T>;
     pdl_wait();
     if (block_flag(skip)) return;
+    W += blockIdx.y * op.ws;            // right-hand side of a batched product
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const int nsf = LS ? kf.ns : op.f2.ns, nsi = LS ? ki.ns : op.i2.ns;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -206,6 +209,9 @@ __global__ void __launch_bounds__(512) k3_rows_inv(OpDev<T> op, const C_t<T>* __
     using C = C_t<T>;
     pdl_wait();
     if (block_flag(skip)) return;
+    W += blockIdx.z * op.ws;            // right-hand side of a batched product
+    u += blockIdx.z * op.xs;
+    y += blockIdx.z * op.xs;
     constexpr FftPlan ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan iv = LS ? ki : op.i1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,6 +256,9 @@ __global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict
     using C = C_t<T>;
     pdl_wait();
     if (block_flag(skip)) return;
+    W += blockIdx.z * op.ws;            // right-hand side of a batched product
+    u += blockIdx.z * op.xs;
+    vbuf += blockIdx.z * op.xs;
     constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
     const FftPlan f = LS ? kf : op.f1;
     const FftPlan iv = LS ? ki : op.i1;
@@ -363,6 +372,8 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
     using F0 = typename PlanStage<C, L, false, 0>::St;
     pdl_wait();
     if (block_flag(skip)) return;
+    u += blockIdx.z * op.xs;            // right-hand side of a batched product
+    W += blockIdx.z * op.ws;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -491,6 +502,7 @@ __global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_f
     const int comp = threadIdx.x >= G ? 1 : 0;
     const int t = threadIdx.x - comp * G;
     C* buf = comp ? buf1 : buf0;
+    W += blockIdx.y * op.ws;            // right-hand side of a batched product
     const int k1 = blockIdx.x;
     C* col = W + ((long)comp * op.M1 + k1) * n2 + t;
     const int h1 = op.M1 >> 1;
@@ -580,6 +592,7 @@ __global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T>
     C* buf1 = buf0 + Lp;
     C* gs = buf1 + Lp;
     const int t = threadIdx.x;
+    W += blockIdx.y * op.ws;            // right-hand side of a batched product
     const int k1 = blockIdx.x;
     C* col0 = W + (long)k1 * n2 + t;
     C* col1 = W + ((long)op.M1 + k1) * n2 + t;
@@ -662,6 +675,9 @@ __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __rest
     using IL = typename PlanStage<C, L, true, ns - 1>::St;
     pdl_wait();
     if (block_flag(skip)) return;
+    W += blockIdx.z * op.ws;            // right-hand side of a batched product
+    u += blockIdx.z * op.xs;
+    y += blockIdx.z * op.xs;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -699,6 +715,9 @@ __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict
     static_assert(IL::kR == F0::kR, "the inverse plan is the reversed forward plan");
     pdl_wait();
     if (block_flag(skip)) return;
+    W += blockIdx.z * op.ws;            // right-hand side of a batched product
+    u += blockIdx.z * op.xs;
+    vbuf += blockIdx.z * op.xs;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int rs = threadIdx.x / G, t = threadIdx.x % G;
@@ -744,6 +763,7 @@ __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict
 
 // --------------------------------------------------------------------- launch
 struct Launch { dim3 grid, block; size_t smem; };
+inline Launch with_z(Launch l, int nb) { l.grid.z = nb; return l; }
 
 template <typename T>
 inline Launch rows_launch(const OpDev<T>& v) {
@@ -811,15 +831,17 @@ template <typename C, int L> inline Launch rows_launch_fast(int n2) {
         default: break;               \
     }
 
+// nb > 1: a batched product over nb right-hand sides (grid z: row passes, grid y: columns).
 template <typename T, typename IO>
-inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st) {
+inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st,
+                      int nb = 1) {
     if (fast_rows(v)) {
-#define K1F_CASE(LSV) { static bool a_ = false; launch_kernel(k1_fast<T, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, u, chi, W, skip); }
+#define K1F_CASE(LSV) { static bool a_ = false; launch_kernel(k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, u, chi, W, skip); }
         DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1F_CASE));
 #undef K1F_CASE
         return;
     }
-    const Launch l = rows_launch(v);
+    const Launch l = with_z(rows_launch(v), nb);
 #define K1_CASE(LSV) { static bool a_ = false; launch_kernel(k1_rows_fwd<T, IO, 16, LSV>, a_, l, st, v, u, chi, W, skip); }
 #define K1_DEF { static bool a16 = false, a12 = false;                                                     \
                  if (v.f1.ept == 16) launch_kernel(k1_rows_fwd<T, IO, 16, 0>, a16, l, st, v, u, chi, W, skip); \
@@ -830,9 +852,10 @@ inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>*
 }
 
 template <typename T>
-inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_t st) {
+inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_t st, int nb = 1) {
     int sg = 0;
-    const Launch l = cols_launch(v, &sg);
+    Launch l = cols_launch(v, &sg);
+    l.grid.y = nb;
     if (fast_cols(v)) {
         if constexpr (sizeof(C_t<T>) == 8) {     // complex64: both components per thread
             const Launch l2{l.grid, dim3(v.M2 / 16), l.smem};
@@ -856,14 +879,15 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
 }
 
 template <typename T, typename U, typename IO>
-inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st) {
+inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st,
+                      int nb = 1) {
     if (fast_rows(v)) {
-#define K3F_CASE(LSV) { static bool a_ = false; launch_kernel(k3_fast<T, U, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, W, u, y, skip); }
+#define K3F_CASE(LSV) { static bool a_ = false; launch_kernel(k3_fast<T, U, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, y, skip); }
         DIE_PROF(PK_ROWS_INV, st, DIE_FAST_SWITCH(v.M1, K3F_CASE));
 #undef K3F_CASE
         return;
     }
-    const Launch l = rows_launch(v);
+    const Launch l = with_z(rows_launch(v), nb);
 #define K3_CASE(LSV) { static bool a_ = false; launch_kernel(k3_rows_inv<T, U, IO, 16, LSV>, a_, l, st, v, W, u, y, skip); }
 #define K3_DEF { static bool a16 = false, a12 = false;                                                    \
                  if (v.f1.ept == 16) launch_kernel(k3_rows_inv<T, U, IO, 16, 0>, a16, l, st, v, W, u, y, skip); \
@@ -875,14 +899,14 @@ inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, con
 
 template <typename T, typename IO>
 inline void launch_k3k1(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
-                        cudaStream_t st) {
+                        cudaStream_t st, int nb = 1) {
     if (fast_rows(v)) {
-#define KKF_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_fast<T, IO, LSV>, a_, rows_launch_fast<C_t<T>, LSV>(v.n2), st, v, W, u, chir, vb, skip); }
+#define KKF_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, chir, vb, skip); }
         DIE_PROF(PK_ROWS_INV_FWD, st, DIE_FAST_SWITCH(v.M1, KKF_CASE));
 #undef KKF_CASE
         return;
     }
-    const Launch l = rows_launch(v);
+    const Launch l = with_z(rows_launch(v), nb);
 #define KK_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_rows<T, IO, 16, LSV>, a_, l, st, v, W, u, chir, vb, skip); }
 #define KK_DEF { static bool a16 = false, a12 = false;                                                        \
                  if (v.f1.ept == 16) launch_kernel(k3k1_rows<T, IO, 16, 0>, a16, l, st, v, W, u, chir, vb, skip); \
@@ -965,6 +989,28 @@ die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st
 template <typename T, typename IO>
 die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st) {
     return apply_reg_skip<T, IO>(op, x, y, nullptr, st);
+}
+
+// nb products y_k = Atilde x_k (Atilde = A_R A when reg, else A) over consecutive field
+// vectors, one launch per pass for all of them, with the caller's workspace (nb sets of
+// row spectra and, when reg, nb middle vectors).
+template <typename T, typename IO>
+die_status apply_batch(dieop_s* op, bool reg, const IO* x, IO* y, int nb, void* Wws, void* vws, cudaStream_t st) {
+    using C = C_t<T>;
+    const OpDev<T> v = Sel<T>::view(op);
+    C* W = reinterpret_cast<C*>(Wws);
+    C* vb = reinterpret_cast<C*>(vws);
+    launch_k1<T, IO>(v, x, Sel<T>::chi(op, Contrast::Chi), W, nullptr, st, nb);
+    launch_k2<T>(v, W, nullptr, st, nb);
+    if (reg) {
+        launch_k3k1<T, IO>(v, W, x, Sel<T>::chi(op, Contrast::ChiReg), vb, nullptr, st, nb);
+        launch_k2<T>(v, W, nullptr, st, nb);
+        launch_k3<T, C, IO>(v, W, vb, y, nullptr, st, nb);
+    } else {
+        launch_k3<T, IO, IO>(v, W, x, y, nullptr, st, nb);
+    }
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
 }
 
 }  // namespace die

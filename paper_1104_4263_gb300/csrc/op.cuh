@@ -15,6 +15,8 @@ struct OpDev {
     const C* tw1;                 // exp(-2 pi i m / M1), m < M1
     const C* tw2;                 // exp(-2 pi i m / M2)
     const C* gq;                  // quarter spectra of G11, G22, G12: [plane][k1q][k2q], pre-scaled
+    long xs;                      // batched products: elements per field vector (2 n1 n2)
+    long ws;                      // batched products: elements per set of row spectra (2 M1 n2)
 };
 
 struct Workspace {
@@ -38,6 +40,8 @@ struct dieop_s {
     double2 *chi_d = nullptr, *chir_d = nullptr;   // chi = eps_r - 1, chi' = 1/eps_r - 1
     float2 *chi_f = nullptr, *chir_f = nullptr;
     die::Workspace ws;             // FP64-sized; the complex64 path uses the first half
+    die::Workspace wsb;            // batched products: grown to the largest batch seen
+    int wsb_cap = 0;
     int* dflag = nullptr;          // device status word (create-time checks)
     uint64_t id = 0;               // identity for deflation handles
     void* solver = nullptr;        // die::SolverCache, created by the first gmres_solve
@@ -63,6 +67,11 @@ template <typename T, typename IO>
 die_status apply_op_skip(dieop_s* op, Contrast c, const IO* x, IO* y, const int* skip, cudaStream_t st);
 template <typename T, typename IO>
 die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st);
+
+// nb products over consecutive field vectors, with a workspace of nb sets of row spectra
+// (Wws) and nb middle vectors (vws, used when reg).
+template <typename T, typename IO>
+die_status apply_batch(dieop_s* op, bool reg, const IO* x, IO* y, int nb, void* Wws, void* vws, cudaStream_t st);
 
 // Input and output of different element types (complex64 in, complex128 out).
 template <typename T, typename IX, typename IY>

@@ -59,6 +59,7 @@ EXPORTS = {
     "dieop_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply_regularized": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply_regularizer": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "dieop_apply_batch": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
     "dieop_rhs_plane_wave": (ct.c_int, [ct.c_void_p, ct.c_double, ct.c_void_p, ct.c_void_p]),
     "dieop_destroy": (None, [ct.c_void_p]),
     "gmres_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p, ct.c_void_p,
@@ -217,6 +218,22 @@ class Operator:
         """y = A(chi') A(chi) x (Eq. (3.19), Section 5)."""
         y = self._out(x, y)
         _check(_lib().dieop_apply_regularized(self._h, _ptr(x), _ptr(y), _stream(stream)), "dieop_apply_regularized")
+        return y
+
+    def apply_batch(self, x, y=None, regularized: bool = False, stream=None):
+        """y_k = A x_k, or A(chi') A(chi) x_k when regularized, for the leading dimension k
+        of x (shape (nrhs, 2, n2, n1)), in one launch per pass."""
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("x must be a contiguous CUDA tensor")
+        if x.dtype != self._io_dtype():
+            raise TypeError(f"expected {self._io_dtype()}, got {x.dtype}")
+        if x.dim() < 1 or x.numel() % (2 * self.N) != 0:
+            raise ValueError("x must hold nrhs field vectors of 2 * n1 * n2 complex values")
+        nrhs = x.numel() // (2 * self.N)
+        y = torch.empty_like(x) if y is None else y
+        _check(_lib().dieop_apply_batch(self._h, nrhs, _ptr(x), _ptr(y), int(bool(regularized)), _stream(stream)),
+               "dieop_apply_batch")
         return y
 
     def apply_regularizer(self, x, y=None, stream=None):

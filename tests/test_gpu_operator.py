@@ -112,6 +112,26 @@ def test_large_grids_match_fft_oracle(n):
     assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), yr) < C64_TOL
 
 
+@pytest.mark.parametrize("n1,n2,prec", [(512, 512, "c64"), (256, 256, "c128"), (128, 200, "c128"), (33, 20, "c64")])
+def test_apply_batch_equals_single_products(n1, n2, prec):
+    """Batched products (one launch per pass over all right-hand sides) are bit-identical
+    to one product per vector, for both the compile-time and the general FFT passes."""
+    rng = W.rng_for(107, n1 * 10000 + n2)
+    eps = W.random_field(rng, n1, n2, lo=1.0, hi=9.0, loss=0.5)
+    h = 2.0 / max(n1, n2)
+    op = die.Operator(eps, h, prec=die.DIE_FP64 if prec == "c128" else die.DIE_FP32_INNER)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    X = torch.stack([dev(W.random_vector(rng, n1, n2), dt) for _ in range(5)])
+    for reg in (False, True):
+        Y = op.apply_batch(X, regularized=reg)
+        for k in range(5):
+            yk = op.apply_regularized(X[k].clone()) if reg else op.apply(X[k].clone())
+            assert torch.equal(Y[k], yk)
+    Yi = X.clone()
+    op.apply_batch(Yi, Yi, regularized=True)
+    assert torch.equal(Yi, op.apply_batch(X, regularized=True))
+
+
 def test_in_place_apply():
     p = W.config1(16)
     rng = W.rng_for(103)

@@ -7,7 +7,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import cylinder, deflation, dense, gmres  # noqa: E402
+from oracle import cylinder, deflation, dense, fftmv, gmres  # noqa: E402
 from paper_1104_4263_gb300 import die, workloads as W  # noqa: E402
 
 
@@ -179,3 +179,25 @@ def test_deflation_for_other_operator_rejected():
         op2.solve(op2.plane_wave(0.0), regularized=True, deflation=D, max_iters=10)
     with pytest.raises(die.DieError):
         op1.solve(op1.plane_wave(0.0), regularized=False, deflation=D, max_iters=10)
+
+
+@pytest.mark.parametrize("inner", [die.DIE_FP32_INNER, die.DIE_FP64])
+def test_full_size_solve_residuals(inner):
+    """512^2 core-shell in the bench's configuration (A_R A P^-1, r = 20, GMRES(30)), three
+    cycles: the residuals the solver reports for the x it returns equal the ones the
+    pinned CPU FFT oracle computes from that x, for the solved system and for A u = b."""
+    p = W.config2(512)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    D = die.Deflation(op, 20, tol=1e-4, regularized=True, inner=inner)
+    x, rep = op.solve(b, restart=30, tol=1e-6, max_iters=90, regularized=True, inner=inner, deflation=D)
+    assert rep["iters"] == 90 and rep["cycles"] == 3
+    xh, bh = x.cpu().numpy(), b.cpu().numpy()
+    assert np.max(np.abs(bh - dense.plane_wave(512, 512, p.h, 0.0))) < 1e-12
+    ref = fftmv.FFTOperator(p.eps_r, p.h, workers=8)
+    bt = ref.apply_R(bh)
+    r_solved = np.linalg.norm(bt - ref.apply_regularized(xh)) / np.linalg.norm(bt)
+    r_orig = np.linalg.norm(bh - ref.apply(xh)) / np.linalg.norm(bh)
+    assert abs(rep["rel_res_solved"] - r_solved) <= 1e-8 * r_solved
+    assert abs(rep["rel_res_orig"] - r_orig) <= 1e-8 * r_orig
+    assert r_solved < 0.5
