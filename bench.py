@@ -371,6 +371,7 @@ def main():
                                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz (FMA probe: 1.255 TFLOP/s)"}
 
     out["matvec"] = matvec_rates(op, p, die, torch)
+    out["batch_solve"] = batch_solve_rates(op, D, die, torch)
     if not args.no_compare:
         out["plain_fp64_same_budget"] = plain_fp64(op, b, args.step_iters, dt / args.steps, last)
         out["time_to_tol"] = time_to_tol(die, W, torch)
@@ -461,6 +462,27 @@ def hbm_peak():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, KeyError):
         return 6800.0
+
+
+def batch_solve_rates(op, D, die, torch, nrhs: int = 4, iters: int = 300):
+    """The timed step's solver on nrhs incidence angles: nrhs sequential gmres_solve calls
+    against one gmres_solve_batch call (concurrent contexts), same step budget each."""
+    B = torch.stack([op.plane_wave(2 * math.pi * k / nrhs) for k in range(nrhs)]).contiguous()
+    kw = dict(restart=RESTART, tol=TOL, max_iters=iters, regularized=True, inner=die.DIE_FP32_INNER, deflation=D)
+    op.solve_batch(B, **kw)                       # contexts allocated, kernels warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = sum(op.solve(B[k].clone(), **kw)[1]["iters"] for k in range(nrhs))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, reps = op.solve_batch(B, **kw)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    steps = sum(r["iters"] for r in reps)
+    return {"nrhs": nrhs, "arnoldi_steps_each": iters, "sequential_per_s": seq / t_seq,
+            "concurrent_per_s": steps / t_bat, "speedup": (steps / t_bat) / (seq / t_seq),
+            "unit": UNIT, "note": "incidence angles 2 pi k / nrhs; wall time around the host calls"}
 
 
 def plain_fp64(op, b, step_iters, step_s, last):

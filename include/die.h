@@ -161,6 +161,20 @@ typedef struct gmres_report {
 die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* opts, const void* b, void* x,
                        gmres_report* report, void* stream);
 
+/* nrhs independent solves with one operator and deflation handle (for example one
+ * scatterer under several incidence angles), run concurrently: b, x hold nrhs complex128
+ * field vectors one after another (vector k at element k * 2 n1 n2); reports: NULL or an
+ * array of nrhs reports (each with its own optional history buffer).  Every right-hand
+ * side gets its own solver context (Krylov basis, product workspace, deflation scratch,
+ * streams, kept by the operator for later calls) and its own host thread, so that the
+ * FP64-bound Gram-Schmidt passes of one system overlap the FFT passes of another.  Each
+ * x_k is bit-identical to gmres_solve on b_k.  The L2 access-policy window of gmres_solve
+ * is not used.  Returns the first error other than DIE_ENOCONV if any, else DIE_ENOCONV
+ * if some system did not converge, else DIE_OK; DIE_EINVAL also for nrhs outside
+ * [1, 16]. */
+die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opts* opts, int nrhs, const void* b, void* x,
+                             gmres_report* reports, void* stream);
+
 /* ----------------------------------------------------------------------------
  * Deflation (Eqs. (4.12)-(4.13)): V = orthonormal basis of the invariant subspace
  * of the r largest-magnitude eigenvalues of Atilde (Krylov-Schur Arnoldi on the

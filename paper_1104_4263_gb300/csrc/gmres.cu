@@ -19,9 +19,12 @@
 // preconditioner, and the FP64 restart residual corrects the iterate).  Arnoldi,
 // least squares and the restart residual are FP64 in both forms.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
+#include <thread>
+#include <vector>
 
 #include "solver.cuh"
 
@@ -52,13 +55,14 @@ void free_red_scratch(RedScratch* rs) {
 
 SolverCache* solver_cache(dieop_s* op) { return reinterpret_cast<SolverCache*>(op->solver); }
 
-void free_solver_cache(dieop_s* op) {
-    SolverCache* c = solver_cache(op);
+static void free_cache(SolverCache* c) {
     if (!c) return;
-    void* ptrs[] = {c->V, c->Vm, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->one};
+    void* ptrs[] = {c->V, c->Vm, c->btil, c->tmp, c->z, c->v32, c->z32, c->small, c->hist, c->ints, c->one,
+                    c->ds.s, c->ds.c32, c->ws.W, c->ws.v};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_red_scratch(&c->rs);
+    free_red_scratch(&c->ds.rs);
     if (c->host) cudaFreeHost(c->host);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : {c->join[0], c->join[1], c->fork, c->back})
@@ -66,24 +70,33 @@ void free_solver_cache(dieop_s* op) {
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->side) cudaStreamDestroy(c->side);
     delete c;
+}
+
+void free_solver_cache(dieop_s* op) {
+    free_cache(solver_cache(op));
     op->solver = nullptr;
+    for (void*& p : op->batch) {
+        free_cache(reinterpret_cast<SolverCache*>(p));
+        p = nullptr;
+    }
 }
 
 // H, cs, sn, g, h1 and h2 (m slots of m+3), y, nrm (2 per step), scale factors, scalars
 static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 2 * (m + 3) + 2 * (size_t)m * (m + 3) + 3 * m + 16; }
 static int ints_count(int m) { return 8 + m; }
 
-die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
-    SolverCache* c = solver_cache(op);
+die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bool own_ws) {
+    SolverCache* c = *slot;
     const long n = 2L * op->N;
     if (c && c->m_cap >= m && c->hist_cap >= hist_cap) return DIE_OK;
     if (c) {
         m = m > c->m_cap ? m : c->m_cap;
         hist_cap = hist_cap > c->hist_cap ? hist_cap : c->hist_cap;
-        free_solver_cache(op);
+        free_cache(c);
+        *slot = nullptr;
     }
     c = new SolverCache();
-    op->solver = c;
+    *slot = c;
     c->m_cap = m;
     c->n = n;
     c->hist_cap = hist_cap;
@@ -94,16 +107,26 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
               al((void**)&c->v32, n * sizeof(float2)) && al((void**)&c->z32, n * sizeof(float2)) &&
               al((void**)&c->small, small_count(m) * sizeof(double2)) &&
               al((void**)&c->hist, (size_t)hist_cap * sizeof(double)) &&
-              al((void**)&c->ints, ints_count(m) * sizeof(int)) && al((void**)&c->one, sizeof(double2));
+              al((void**)&c->ints, ints_count(m) * sizeof(int)) && al((void**)&c->one, sizeof(double2)) &&
+              al((void**)&c->ds.s, (size_t)(kMaxBasis + 2) * sizeof(double2)) &&
+              al((void**)&c->ds.c32, (size_t)kMaxBasis * sizeof(float2));
+    if (ok && own_ws) {
+        c->ws.W_bytes = op->ws.W_bytes;
+        c->ws.v_bytes = op->ws.v_bytes;
+        ok = al(&c->ws.W, c->ws.W_bytes) && al(&c->ws.v, c->ws.v_bytes);
+    }
     if (!ok) {
         cudaGetLastError();
-        free_solver_cache(op);
+        free_cache(c);
+        *slot = nullptr;
         return DIE_ENOMEM;
     }
     DIE_TRY(alloc_red_scratch(&c->rs));
+    DIE_TRY(alloc_red_scratch(&c->ds.rs));
     if (cudaHostAlloc((void**)&c->host, 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
-        free_solver_cache(op);
+        free_cache(c);
+        *slot = nullptr;
         return DIE_ENOMEM;
     }
     const double2 one = make_double2(1.0, 0.0);
@@ -118,31 +141,46 @@ die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
     return DIE_OK;
 }
 
-die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live) {
-    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, 0, d->s, d->rs, skip, st, live));
-    DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, d->s, x, z, d->n, skip, st));
+die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap) {
+    SolverCache* c = solver_cache(op);
+    const die_status s = ensure_cache(&c, op, m, hist_cap, false);
+    op->solver = c;
+    return s;
+}
+
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live,
+                      const DeflScratch* sc) {
+    double2* s = sc ? sc->s : d->s;
+    const RedScratch& rs = sc ? sc->rs : d->rs;
+    DIE_TRY(k_dots(d->V, d->n, d->r, x, d->n, 0, s, rs, skip, st, live));
+    DIE_TRY(k_defl_update(d->V, d->n, d->r, d->M, s, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
 die_status defl_apply32(defl_s* d, float2* x, double2* w, const double* inv, float2* z, const int* skip,
-                        cudaStream_t st, bool live) {
-    DIE_TRY(k_dots32(d->V32, d->n, d->r, x, w, inv, d->n, d->s, d->M32, d->c32, d->rs, skip, st, live));
-    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, d->c32, x, z, d->n, skip, st));
+                        cudaStream_t st, bool live, const DeflScratch* sc) {
+    double2* s = sc ? sc->s : d->s;
+    float2* c32 = sc ? sc->c32 : d->c32;
+    const RedScratch& rs = sc ? sc->rs : d->rs;
+    DIE_TRY(k_dots32(d->V32, d->n, d->r, x, w, inv, d->n, s, d->M32, c32, rs, skip, st, live));
+    DIE_TRY(k_defl_update32(d->V32, d->n, d->r, c32, x, z, d->n, skip, st));
     return DIE_OK;
 }
 
 // Atilde in FP64 (restart residuals, right-hand side).
-static die_status apply64(dieop_s* op, bool reg, const double2* in, double2* out, cudaStream_t st) {
-    return reg ? apply_reg<double, double2>(op, in, out, st) : apply_op<double, double2>(op, Contrast::Chi, in, out, st);
+static die_status apply64(dieop_s* op, bool reg, const double2* in, double2* out, cudaStream_t st,
+                          const Workspace* ws) {
+    return reg ? apply_reg<double, double2>(op, in, out, st, ws)
+               : apply_op<double, double2>(op, Contrast::Chi, in, out, st, ws);
 }
 
 static die_status apply_inner(dieop_s* op, bool reg, bool mixed, const double2* in, double2* out, const int* skip,
-                              cudaStream_t st) {
+                              cudaStream_t st, const Workspace* ws) {
     if (mixed)
-        return reg ? apply_reg_skip<float, double2>(op, in, out, skip, st)
-                   : apply_op_skip<float, double2>(op, Contrast::Chi, in, out, skip, st);
-    return reg ? apply_reg_skip<double, double2>(op, in, out, skip, st)
-               : apply_op_skip<double, double2>(op, Contrast::Chi, in, out, skip, st);
+        return reg ? apply_reg_skip<float, double2>(op, in, out, skip, st, ws)
+                   : apply_op_skip<float, double2>(op, Contrast::Chi, in, out, skip, st, ws);
+    return reg ? apply_reg_skip<double, double2>(op, in, out, skip, st, ws)
+               : apply_op_skip<double, double2>(op, Contrast::Chi, in, out, skip, st, ws);
 }
 
 // ||v||^2 read back to the host (synchronises the stream).
@@ -164,6 +202,8 @@ struct L2Pin {
     size_t old_limit = 0;
     L2Pin(cudaStream_t s, const void* base, size_t bytes) : st(s) {
         int dev = 0, max_persist = 0, max_window = 0;
+        const char* env = getenv("DIE_L2PIN");
+        if (env && env[0] == '0') return;        // DIE_L2PIN=0: no window (A/B timing)
         if (!base || bytes == 0 || cudaGetDevice(&dev) != cudaSuccess) return;
         if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
@@ -207,22 +247,28 @@ static double seconds_since(std::chrono::steady_clock::time_point t0) {
 
 using namespace die;
 
-extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, const void* b_, void* x_,
-                                  gmres_report* rep, void* stream) {
-    if (!op || !o || !b_ || !x_) return DIE_EINVAL;
-    if (o->restart < 1 || o->restart > 256 || o->max_iters < 0 || !(o->tol >= 0)) return DIE_EINVAL;
-    if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return DIE_EINVAL;
-    if (defl && (defl->op_id != op->id || defl->regularized != (o->regularized ? 1 : 0))) return DIE_EINVAL;
+static bool opts_valid(const dieop_s* op, const defl_s* defl, const gmres_opts* o) {
+    if (o->restart < 1 || o->restart > 256 || o->max_iters < 0 || !(o->tol >= 0)) return false;
+    if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return false;
+    if (defl && (defl->op_id != op->id || defl->regularized != (o->regularized ? 1 : 0))) return false;
+    return true;
+}
+
+static int hist_cap_of(const gmres_opts* o) {
+    return o->max_iters < (1 << 22) ? (o->max_iters > 0 ? o->max_iters : 1) : (1 << 22);
+}
+
+// One solve in context c (its buffers, streams, deflation scratch and, for a batch
+// context, its product workspace); pin: use the L2 window for the deflation basis.
+static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, const void* b_, void* x_,
+                            gmres_report* rep, cudaStream_t ust, SolverCache* c, bool pin) {
     const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t ust = (cudaStream_t)stream;
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
     const double eta = o->reorth_eta > 0 ? o->reorth_eta : 0.01;
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
     const int m = o->restart;
     const long n = 2L * op->N;
-    const int hist_cap = o->max_iters < (1 << 22) ? (o->max_iters > 0 ? o->max_iters : 1) : (1 << 22);
-    DIE_TRY(ensure_solver_cache(op, m, hist_cap));
-    SolverCache* c = solver_cache(op);
+    const Workspace* pws = c->ws.W ? &c->ws : nullptr;
     // The solve runs on the library's own stream, ordered after the caller's stream at
     // entry and before it at every exit (a stream of its own can carry the L2
     // access-policy window below, which the legacy default stream cannot).
@@ -271,7 +317,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     const double2* bt = b;
     int n_apply = 0;
     if (reg) {
-        DIE_TRY(apply_op<double, double2>(op, Contrast::ChiReg, b, c->btil, st));
+        DIE_TRY(apply_op<double, double2>(op, Contrast::ChiReg, b, c->btil, st, pws));
         bt = c->btil;
         n_apply++;
     }
@@ -307,11 +353,11 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         dp.ld = n;
         dp.r = defl->r;
         dp.M32 = defl->M32;
-        dp.s = defl->s;
-        dp.cf = defl->c32;
+        dp.s = c->ds.s;
+        dp.cf = c->ds.c32;
     }
     // the complex64 deflation basis is read twice per Arnoldi step: keep it in L2
-    L2Pin pin(st, defl32 ? defl->V32 : nullptr, defl32 ? (size_t)defl->r * n * sizeof(float2) : 0);
+    L2Pin l2pin(st, pin && defl32 ? defl->V32 : nullptr, defl32 ? (size_t)defl->r * n * sizeof(float2) : 0);
     if (bnorm == 0.0) {
         DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
         status = DIE_OK;
@@ -321,7 +367,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (cycles == 0 && !o->use_x0) {
             DIE_CUDA_TRY(cudaMemcpyAsync(V, bt, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         } else {
-            DIE_TRY(apply64(op, reg, x, c->tmp, st));
+            DIE_TRY(apply64(op, reg, x, c->tmp, st, pws));
             n_apply += reg ? 2 : 1;
             DIE_TRY(k_sub(bt, c->tmp, V, n, st));
         }
@@ -333,8 +379,8 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         if (iters >= o->max_iters) break;
         DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32, Vm));
         if (fold)   // cf for v_0
-            DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, defl->s, defl->M32, defl->c32,
-                             defl->rs, nullptr, st));
+            DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, c->ds.s, defl->M32, c->ds.c32,
+                             c->ds.rs, nullptr, st));
         DIE_TRY(k_gmres_init(S, scal, st));
         const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
         S.jmax = jmax;
@@ -352,33 +398,33 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
                 din.V32 = defl->V32;
                 din.ld = n;
                 din.r = defl->r;
-                din.cf = defl->c32;
+                din.cf = c->ds.c32;
                 din.x = c->v32;
                 din.w = j > 0 ? vj : nullptr;
                 din.inv = inv_prev;
                 din.wm = j > 0 && Vm ? Vm + (long)j * ldv : nullptr;
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
-                DIE_TRY(apply_defl_xy(op, din, c->z32, w, reg, S.done, st));
+                DIE_TRY(apply_defl_xy(op, din, c->z32, w, reg, S.done, st, pws));
             } else if (fold) {
-                DIE_TRY(k_defl_update32(defl->V32, n, defl->r, defl->c32, c->v32, c->z32, n, S.done, st,
+                DIE_TRY(k_defl_update32(defl->V32, n, defl->r, c->ds.c32, c->v32, c->z32, n, S.done, st,
                                         j > 0 ? vj : nullptr, inv_prev, j > 0 && Vm ? Vm + (long)j * ldv : nullptr));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
-                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
-                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
+                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st, pws)
+                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st, pws));
             } else if (defl32) {
-                DIE_TRY(defl_apply32(defl, c->v32, j > 0 ? vj : nullptr, inv_prev, c->z32, S.done, st, true));
+                DIE_TRY(defl_apply32(defl, c->v32, j > 0 ? vj : nullptr, inv_prev, c->z32, S.done, st, true, &c->ds));
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
-                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st)
-                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st));
+                DIE_TRY(reg ? apply_reg_skip_xy<float, float2, double2>(op, c->z32, w, S.done, st, pws)
+                            : apply_op_skip_xy<float, float2, double2>(op, Contrast::Chi, c->z32, w, S.done, st, pws));
             } else {
                 if (inv_prev) DIE_TRY(k_scale_by(vj, n, inv_prev, S.done, st, nullptr, Vm ? Vm + (long)j * ldv : nullptr));
                 const double2* src = vj;
                 if (defl) {
-                    DIE_TRY(defl_apply(defl, vj, c->z, S.done, st, true));
+                    DIE_TRY(defl_apply(defl, vj, c->z, S.done, st, true, &c->ds));
                     src = c->z;
                 }
                 if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 1], st));
-                DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st));
+                DIE_TRY(apply_inner(op, reg, mixed, src, w, S.done, st, pws));
             }
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
             DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1 + (long)j * (m + 3), S.h2 + (long)j * (m + 3), S.nrm + 2 * j,
@@ -414,7 +460,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         DIE_TRY(k_gmres_lsq(S, st));
         if (defl) {
             DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, nullptr, c->tmp, n, nullptr, nullptr, c->rs, nullptr, st));
-            DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st));
+            DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st, false, &c->ds));
             DIE_TRY(k_basis_axpy(c->tmp, ldv, 1, c->one, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
         } else {
             DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
@@ -427,7 +473,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
     }
     double rel_orig = rel;
     if (reg && (status == DIE_OK || status == DIE_ENOCONV)) {
-        DIE_TRY(apply_op<double, double2>(op, Contrast::Chi, x, c->tmp, st));
+        DIE_TRY(apply_op<double, double2>(op, Contrast::Chi, x, c->tmp, st, pws));
         n_apply++;
         DIE_TRY(k_sub(b, c->tmp, c->tmp, n, st));
         double r2 = 0, b2 = 0;
@@ -457,4 +503,47 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
         }
     }
     return status;
+}
+
+extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, const void* b_, void* x_,
+                                  gmres_report* rep, void* stream) {
+    if (!op || !o || !b_ || !x_) return DIE_EINVAL;
+    if (!opts_valid(op, defl, o)) return DIE_EINVAL;
+    DIE_TRY(ensure_solver_cache(op, o->restart, hist_cap_of(o)));
+    return solve_ctx(op, defl, o, b_, x_, rep, (cudaStream_t)stream, solver_cache(op), true);
+}
+
+// Right-hand sides solved concurrently: one context (buffers, product workspace, deflation
+// scratch, streams) and one host thread per right-hand side, so that the FP64-bound
+// Gram-Schmidt passes of one system and the FFT passes of another share the GPU.
+extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opts* o, int nrhs, const void* b_,
+                                        void* x_, gmres_report* reps, void* stream) {
+    if (!op || !o || !b_ || !x_ || nrhs < 1 || nrhs > kMaxBatchSolve) return DIE_EINVAL;
+    if (!opts_valid(op, defl, o)) return DIE_EINVAL;
+    const long n = 2L * op->N;
+    for (int k = 0; k < nrhs; k++) {
+        SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[k]);
+        const die_status s = ensure_cache(&c, op, o->restart, hist_cap_of(o), true);
+        op->batch[k] = c;
+        if (s != DIE_OK) return s;
+    }
+    int dev = 0;
+    DIE_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<die_status> status(nrhs, DIE_OK);
+    std::vector<std::thread> threads;
+    threads.reserve(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+        threads.emplace_back([&, k] {
+            if (cudaSetDevice(dev) != cudaSuccess) { status[k] = DIE_ECUDA; return; }
+            status[k] = solve_ctx(op, defl, o, (const double2*)b_ + k * n, (double2*)x_ + k * n,
+                                  reps ? reps + k : nullptr, (cudaStream_t)stream,
+                                  reinterpret_cast<SolverCache*>(op->batch[k]), false);
+        });
+    }
+    for (auto& t : threads) t.join();
+    die_status out = DIE_OK;
+    for (die_status s : status)
+        if (s != DIE_OK && s != DIE_ENOCONV) return s;
+        else if (s == DIE_ENOCONV) out = DIE_ENOCONV;
+    return out;
 }

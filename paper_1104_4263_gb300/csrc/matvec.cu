@@ -25,10 +25,14 @@ OpDev<float> view_f(const dieop_s* op) {
 // Shared-memory limits are raised lazily by each launcher on first use.
 die_status set_kernel_attributes(const dieop_s*) { return DIE_OK; }
 
-template die_status apply_op<double, double2>(dieop_s*, Contrast, const double2*, double2*, cudaStream_t);
-template die_status apply_reg<double, double2>(dieop_s*, const double2*, double2*, cudaStream_t);
-template die_status apply_op_skip<double, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t);
-template die_status apply_reg_skip<double, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t);
+template die_status apply_op<double, double2>(dieop_s*, Contrast, const double2*, double2*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_reg<double, double2>(dieop_s*, const double2*, double2*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_op_skip<double, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_reg_skip<double, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t,
+                                  const Workspace*);
 template die_status apply_batch<double, double2>(dieop_s*, bool, const double2*, double2*, int, void*, void*,
                                                  cudaStream_t);
 

@@ -5,28 +5,37 @@
 
 namespace die {
 
-template die_status apply_op<float, float2>(dieop_s*, Contrast, const float2*, float2*, cudaStream_t);
-template die_status apply_op<float, double2>(dieop_s*, Contrast, const double2*, double2*, cudaStream_t);
-template die_status apply_reg<float, float2>(dieop_s*, const float2*, float2*, cudaStream_t);
-template die_status apply_reg<float, double2>(dieop_s*, const double2*, double2*, cudaStream_t);
+template die_status apply_op<float, float2>(dieop_s*, Contrast, const float2*, float2*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_op<float, double2>(dieop_s*, Contrast, const double2*, double2*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_reg<float, float2>(dieop_s*, const float2*, float2*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_reg<float, double2>(dieop_s*, const double2*, double2*, cudaStream_t,
+                                  const Workspace*);
 template die_status apply_batch<float, float2>(dieop_s*, bool, const float2*, float2*, int, void*, void*, cudaStream_t);
-template die_status apply_op_skip<float, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t);
-template die_status apply_reg_skip<float, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t);
+template die_status apply_op_skip<float, double2>(dieop_s*, Contrast, const double2*, double2*, const int*, cudaStream_t,
+                                  const Workspace*);
+template die_status apply_reg_skip<float, double2>(dieop_s*, const double2*, double2*, const int*, cudaStream_t,
+                                  const Workspace*);
 template die_status apply_op_skip_xy<float, float2, double2>(dieop_s*, Contrast, const float2*, double2*, const int*,
-                                                             cudaStream_t);
+                                                             cudaStream_t,
+                                  const Workspace*);
 template die_status apply_reg_skip_xy<float, float2, double2>(dieop_s*, const float2*, double2*, const int*,
-                                                              cudaStream_t);
+                                                              cudaStream_t,
+                                  const Workspace*);
 
 bool defl_product_ok(const dieop_s* op) { return fast_rows(view_f(op)); }
 
 die_status apply_defl_xy(dieop_s* op, const DeflIn& d, float2* z, double2* y, bool reg, const int* skip,
-                         cudaStream_t st) {
+                         cudaStream_t st, const Workspace* ws) {
+    if (!ws) ws = &op->ws;
     const OpDev<float> v = view_f(op);
     if (!fast_rows(v) || d.r < 1 || d.r > 32 || !d.V32 || !d.cf || (!d.w && !d.x) || (d.w && !d.inv))
         return DIE_EINVAL;
-    float2* W = reinterpret_cast<float2*>(op->ws.W);
-    float2* vb = reinterpret_cast<float2*>(op->ws.v);
-#define K1D_CASE(LSV) { static bool a_ = false; launch_kernel(k1_defl_fast<LSV>, a_, rows_launch_fast<float2, LSV>(v.n2), st, v, d, op->chi_f, z, W, skip); }
+    float2* W = reinterpret_cast<float2*>(ws->W);
+    float2* vb = reinterpret_cast<float2*>(ws->v);
+#define K1D_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k1_defl_fast<LSV>, a_, rows_launch_fast<float2, LSV>(v.n2), st, v, d, op->chi_f, z, W, skip); }
     DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1D_CASE));
 #undef K1D_CASE
     launch_k2<float>(v, W, skip, st);

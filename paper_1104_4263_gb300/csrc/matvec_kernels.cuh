@@ -25,6 +25,8 @@
 // compile time so that radices, strides and indices are constants.
 #pragma once
 
+#include <atomic>
+
 #include "fft_fast.cuh"
 #include "op.cuh"
 #include "prof.cuh"
@@ -786,12 +788,12 @@ inline Launch cols_launch(const OpDev<T>& v, int* stage_g) {
 // Launch a kernel instantiation, raising its dynamic shared-memory limit on first use
 // to what the 227 KB per block leaves beside the kernel's static shared memory.
 template <typename K, typename... Args>
-inline void launch_kernel(K kernel, bool& attr_set, const Launch& l, cudaStream_t st, Args... args) {
-    if (!attr_set) {
+inline void launch_kernel(K kernel, std::atomic<bool>& attr_set, const Launch& l, cudaStream_t st, Args... args) {
+    if (!attr_set.load(std::memory_order_acquire)) {
         cudaFuncAttributes fa = {};
         const size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
-        attr_set = true;
+        attr_set.store(true, std::memory_order_release);
     }
     launch_pdl(kernel, l.grid, l.block, l.smem, st, args...);
 }
@@ -836,14 +838,14 @@ template <typename T, typename IO>
 inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st,
                       int nb = 1) {
     if (fast_rows(v)) {
-#define K1F_CASE(LSV) { static bool a_ = false; launch_kernel(k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, u, chi, W, skip); }
+#define K1F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, u, chi, W, skip); }
         DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1F_CASE));
 #undef K1F_CASE
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);
-#define K1_CASE(LSV) { static bool a_ = false; launch_kernel(k1_rows_fwd<T, IO, 16, LSV>, a_, l, st, v, u, chi, W, skip); }
-#define K1_DEF { static bool a16 = false, a12 = false;                                                     \
+#define K1_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k1_rows_fwd<T, IO, 16, LSV>, a_, l, st, v, u, chi, W, skip); }
+#define K1_DEF { static std::atomic<bool> a16{false}, a12{false};                                                     \
                  if (v.f1.ept == 16) launch_kernel(k1_rows_fwd<T, IO, 16, 0>, a16, l, st, v, u, chi, W, skip); \
                  else launch_kernel(k1_rows_fwd<T, IO, 12, 0>, a12, l, st, v, u, chi, W, skip); }
     DIE_PROF(PK_ROWS_FWD, st, DIE_POW2_SWITCH(v.M1, K1_CASE, K1_DEF));
@@ -859,18 +861,18 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
     if (fast_cols(v)) {
         if constexpr (sizeof(C_t<T>) == 8) {     // complex64: both components per thread
             const Launch l2{l.grid, dim3(v.M2 / 16), l.smem};
-#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast2<T, LSV>, a_, l2, st, v, W, sg, skip); }
+#define K2F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k2_fast2<T, LSV>, a_, l2, st, v, W, sg, skip); }
             DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
 #undef K2F_CASE
         } else {
-#define K2F_CASE(LSV) { static bool a_ = false; launch_kernel(k2_fast<T, LSV>, a_, l, st, v, W, sg, skip); }
+#define K2F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k2_fast<T, LSV>, a_, l, st, v, W, sg, skip); }
             DIE_PROF(PK_COLS, st, DIE_FAST_SWITCH(v.M2, K2F_CASE));
 #undef K2F_CASE
         }
         return;
     }
-#define K2_CASE(LSV) { static bool a_ = false; launch_kernel(k2_cols<T, 16, LSV>, a_, l, st, v, W, sg, skip); }
-#define K2_DEF { static bool a16 = false, a12 = false;                                            \
+#define K2_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k2_cols<T, 16, LSV>, a_, l, st, v, W, sg, skip); }
+#define K2_DEF { static std::atomic<bool> a16{false}, a12{false};                                            \
                  if (v.f2.ept == 16) launch_kernel(k2_cols<T, 16, 0>, a16, l, st, v, W, sg, skip); \
                  else launch_kernel(k2_cols<T, 12, 0>, a12, l, st, v, W, sg, skip); }
     DIE_PROF(PK_COLS, st, DIE_POW2_SWITCH(v.M2, K2_CASE, K2_DEF));
@@ -882,14 +884,14 @@ template <typename T, typename U, typename IO>
 inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st,
                       int nb = 1) {
     if (fast_rows(v)) {
-#define K3F_CASE(LSV) { static bool a_ = false; launch_kernel(k3_fast<T, U, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, y, skip); }
+#define K3F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3_fast<T, U, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, y, skip); }
         DIE_PROF(PK_ROWS_INV, st, DIE_FAST_SWITCH(v.M1, K3F_CASE));
 #undef K3F_CASE
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);
-#define K3_CASE(LSV) { static bool a_ = false; launch_kernel(k3_rows_inv<T, U, IO, 16, LSV>, a_, l, st, v, W, u, y, skip); }
-#define K3_DEF { static bool a16 = false, a12 = false;                                                    \
+#define K3_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3_rows_inv<T, U, IO, 16, LSV>, a_, l, st, v, W, u, y, skip); }
+#define K3_DEF { static std::atomic<bool> a16{false}, a12{false};                                                    \
                  if (v.f1.ept == 16) launch_kernel(k3_rows_inv<T, U, IO, 16, 0>, a16, l, st, v, W, u, y, skip); \
                  else launch_kernel(k3_rows_inv<T, U, IO, 12, 0>, a12, l, st, v, W, u, y, skip); }
     DIE_PROF(PK_ROWS_INV, st, DIE_POW2_SWITCH(v.M1, K3_CASE, K3_DEF));
@@ -901,14 +903,14 @@ template <typename T, typename IO>
 inline void launch_k3k1(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
                         cudaStream_t st, int nb = 1) {
     if (fast_rows(v)) {
-#define KKF_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, chir, vb, skip); }
+#define KKF_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, chir, vb, skip); }
         DIE_PROF(PK_ROWS_INV_FWD, st, DIE_FAST_SWITCH(v.M1, KKF_CASE));
 #undef KKF_CASE
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);
-#define KK_CASE(LSV) { static bool a_ = false; launch_kernel(k3k1_rows<T, IO, 16, LSV>, a_, l, st, v, W, u, chir, vb, skip); }
-#define KK_DEF { static bool a16 = false, a12 = false;                                                        \
+#define KK_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3k1_rows<T, IO, 16, LSV>, a_, l, st, v, W, u, chir, vb, skip); }
+#define KK_DEF { static std::atomic<bool> a16{false}, a12{false};                                                        \
                  if (v.f1.ept == 16) launch_kernel(k3k1_rows<T, IO, 16, 0>, a16, l, st, v, W, u, chir, vb, skip); \
                  else launch_kernel(k3k1_rows<T, IO, 12, 0>, a12, l, st, v, W, u, chir, vb, skip); }
     DIE_PROF(PK_ROWS_INV_FWD, st, DIE_POW2_SWITCH(v.M1, KK_CASE, KK_DEF));
@@ -927,10 +929,12 @@ template <> struct Sel<float> {
 };
 
 template <typename T, typename IO>
-die_status apply_op_skip(dieop_s* op, Contrast which, const IO* x, IO* y, const int* skip, cudaStream_t st) {
+die_status apply_op_skip(dieop_s* op, Contrast which, const IO* x, IO* y, const int* skip, cudaStream_t st,
+                         const Workspace* ws) {
+    if (!ws) ws = &op->ws;
     using C = C_t<T>;
     const OpDev<T> v = Sel<T>::view(op);
-    C* W = reinterpret_cast<C*>(op->ws.W);
+    C* W = reinterpret_cast<C*>(ws->W);
     launch_k1<T, IO>(v, x, Sel<T>::chi(op, which), W, skip, st);
     launch_k2<T>(v, W, skip, st);
     launch_k3<T, IO, IO>(v, W, x, y, skip, st);
@@ -939,11 +943,12 @@ die_status apply_op_skip(dieop_s* op, Contrast which, const IO* x, IO* y, const 
 }
 
 template <typename T, typename IO>
-die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st) {
+die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st, const Workspace* ws) {
+    if (!ws) ws = &op->ws;
     using C = C_t<T>;
     const OpDev<T> v = Sel<T>::view(op);
-    C* W = reinterpret_cast<C*>(op->ws.W);
-    C* vb = reinterpret_cast<C*>(op->ws.v);
+    C* W = reinterpret_cast<C*>(ws->W);
+    C* vb = reinterpret_cast<C*>(ws->v);
     launch_k1<T, IO>(v, x, Sel<T>::chi(op, Contrast::Chi), W, skip, st);
     launch_k2<T>(v, W, skip, st);
     launch_k3k1<T, IO>(v, W, x, Sel<T>::chi(op, Contrast::ChiReg), vb, skip, st);
@@ -956,10 +961,12 @@ die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cuda
 // Input and output of different element types (complex64 in, complex128 out: the
 // products of the FP32-inner solves whose right preconditioner runs in complex64).
 template <typename T, typename IX, typename IY>
-die_status apply_op_skip_xy(dieop_s* op, Contrast which, const IX* x, IY* y, const int* skip, cudaStream_t st) {
+die_status apply_op_skip_xy(dieop_s* op, Contrast which, const IX* x, IY* y, const int* skip, cudaStream_t st,
+                            const Workspace* ws) {
+    if (!ws) ws = &op->ws;
     using C = C_t<T>;
     const OpDev<T> v = Sel<T>::view(op);
-    C* W = reinterpret_cast<C*>(op->ws.W);
+    C* W = reinterpret_cast<C*>(ws->W);
     launch_k1<T, IX>(v, x, Sel<T>::chi(op, which), W, skip, st);
     launch_k2<T>(v, W, skip, st);
     launch_k3<T, IX, IY>(v, W, x, y, skip, st);
@@ -968,11 +975,13 @@ die_status apply_op_skip_xy(dieop_s* op, Contrast which, const IX* x, IY* y, con
 }
 
 template <typename T, typename IX, typename IY>
-die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st) {
+die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st,
+                             const Workspace* ws) {
+    if (!ws) ws = &op->ws;
     using C = C_t<T>;
     const OpDev<T> v = Sel<T>::view(op);
-    C* W = reinterpret_cast<C*>(op->ws.W);
-    C* vb = reinterpret_cast<C*>(op->ws.v);
+    C* W = reinterpret_cast<C*>(ws->W);
+    C* vb = reinterpret_cast<C*>(ws->v);
     launch_k1<T, IX>(v, x, Sel<T>::chi(op, Contrast::Chi), W, skip, st);
     launch_k2<T>(v, W, skip, st);
     launch_k3k1<T, IX>(v, W, x, Sel<T>::chi(op, Contrast::ChiReg), vb, skip, st);
@@ -983,12 +992,12 @@ die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, c
 }
 
 template <typename T, typename IO>
-die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st) {
-    return apply_op_skip<T, IO>(op, c, x, y, nullptr, st);
+die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st, const Workspace* ws) {
+    return apply_op_skip<T, IO>(op, c, x, y, nullptr, st, ws);
 }
 template <typename T, typename IO>
-die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st) {
-    return apply_reg_skip<T, IO>(op, x, y, nullptr, st);
+die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st, const Workspace* ws) {
+    return apply_reg_skip<T, IO>(op, x, y, nullptr, st, ws);
 }
 
 // nb products y_k = Atilde x_k (Atilde = A_R A when reg, else A) over consecutive field

@@ -45,6 +45,7 @@ struct dieop_s {
     int* dflag = nullptr;          // device status word (create-time checks)
     uint64_t id = 0;               // identity for deflation handles
     void* solver = nullptr;        // die::SolverCache, created by the first gmres_solve
+    void* batch[16] = {};          // die::SolverCache of each right-hand side of gmres_solve_batch
 };
 
 namespace die {
@@ -54,19 +55,23 @@ OpDev<float> view_f(const dieop_s* op);
 
 enum class Contrast { Chi, ChiReg };
 
-// y = (I - G X(contrast)) x with compute type T and element type IO for x and y.
+// y = (I - G X(contrast)) x with compute type T and element type IO for x and y.  Every
+// product takes an optional workspace (row spectra W, middle vector v); NULL = the
+// operator's own (op->ws).  Concurrent products on one operator need one each.
 template <typename T, typename IO>
-die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st);
+die_status apply_op(dieop_s* op, Contrast c, const IO* x, IO* y, cudaStream_t st, const Workspace* ws = nullptr);
 
 // y = A(chi') A(chi) x.
 template <typename T, typename IO>
-die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st);
+die_status apply_reg(dieop_s* op, const IO* x, IO* y, cudaStream_t st, const Workspace* ws = nullptr);
 
 // The same with a device flag: every kernel returns at once when *skip != 0.
 template <typename T, typename IO>
-die_status apply_op_skip(dieop_s* op, Contrast c, const IO* x, IO* y, const int* skip, cudaStream_t st);
+die_status apply_op_skip(dieop_s* op, Contrast c, const IO* x, IO* y, const int* skip, cudaStream_t st,
+                         const Workspace* ws = nullptr);
 template <typename T, typename IO>
-die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st);
+die_status apply_reg_skip(dieop_s* op, const IO* x, IO* y, const int* skip, cudaStream_t st,
+                          const Workspace* ws = nullptr);
 
 // nb products over consecutive field vectors, with a workspace of nb sets of row spectra
 // (Wws) and nb middle vectors (vws, used when reg).
@@ -75,9 +80,11 @@ die_status apply_batch(dieop_s* op, bool reg, const IO* x, IO* y, int nb, void* 
 
 // Input and output of different element types (complex64 in, complex128 out).
 template <typename T, typename IX, typename IY>
-die_status apply_op_skip_xy(dieop_s* op, Contrast c, const IX* x, IY* y, const int* skip, cudaStream_t st);
+die_status apply_op_skip_xy(dieop_s* op, Contrast c, const IX* x, IY* y, const int* skip, cudaStream_t st,
+                            const Workspace* ws = nullptr);
 template <typename T, typename IX, typename IY>
-die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st);
+die_status apply_reg_skip_xy(dieop_s* op, const IX* x, IY* y, const int* skip, cudaStream_t st,
+                             const Workspace* ws = nullptr);
 
 // Input of a product whose first row pass also applies the deflation preconditioner of
 // the FP32-inner solves: z = v + V32 cf, with v = w * (*inv) (the FP64 Arnoldi vector,
@@ -97,7 +104,7 @@ struct DeflIn {
 // compile-time FFT path along x1 (defl_product_ok).
 bool defl_product_ok(const dieop_s* op);
 die_status apply_defl_xy(dieop_s* op, const DeflIn& d, float2* z, double2* y, bool reg, const int* skip,
-                         cudaStream_t st);
+                         cudaStream_t st, const Workspace* ws = nullptr);
 
 die_status set_kernel_attributes(const dieop_s* op);
 

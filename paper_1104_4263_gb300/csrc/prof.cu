@@ -7,7 +7,7 @@
 namespace die {
 
 bool g_prof_on = false;
-int g_prof_override = -1;
+thread_local int g_prof_override = -1;
 
 namespace {
 struct Rec {

@@ -27,7 +27,7 @@ enum ProfKernel {
 };
 
 extern bool g_prof_on;
-extern int g_prof_override;      // >= 0: record launches under this class instead
+extern thread_local int g_prof_override;      // >= 0: record launches under this class instead
 void prof_mark(int id, cudaStream_t st, int stop);
 
 }  // namespace die

@@ -8,7 +8,19 @@
 
 namespace die {
 
-// Device buffers reused across gmres_solve calls on one operator.
+// Scratch of one deflation apply: projections (r + 2), complex64 coefficients (r) and
+// the reduction scratch.  A solver context owns one, so that concurrent solves can share
+// a deflation handle.
+struct DeflScratch {
+    double2* s = nullptr;
+    float2* c32 = nullptr;
+    RedScratch rs;
+};
+
+constexpr int kMaxBatchSolve = 16;   // right-hand sides of one gmres_solve_batch call
+
+// Device buffers reused across gmres_solve calls on one operator (one context), or by one
+// right-hand side of gmres_solve_batch (a batch context, with its own product workspace).
 struct SolverCache {
     int m_cap = 0;          // Krylov dimension the buffers hold
     long n = 0;             // vector length 2N
@@ -31,11 +43,16 @@ struct SolverCache {
     cudaStream_t side = nullptr;    // Givens steps, one step behind the Arnoldi steps
     cudaEvent_t join[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, back = nullptr;   // stream -> side, side -> stream
+    DeflScratch ds;                 // deflation scratch (kMaxBasis + 2 projections)
+    Workspace ws;                   // batch contexts: own product workspace (else W == NULL)
 };
 
-void free_solver_cache(dieop_s* op);
+void free_solver_cache(dieop_s* op);   // the operator's context and its batch contexts
 SolverCache* solver_cache(dieop_s* op);
 die_status ensure_solver_cache(dieop_s* op, int m, int hist_cap);
+// A context in *slot with room for GMRES(m) and hist_cap history entries; own_ws: with
+// its own product workspace.
+die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bool own_ws);
 die_status alloc_red_scratch(RedScratch* rs);
 void free_red_scratch(RedScratch* rs);
 
@@ -58,10 +75,12 @@ struct defl_s {
 };
 
 namespace die {
-// z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip`, `live` as for the Krylov kernels.
-die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live = false);
+// z = P^-1 x = x + V (M (V^* x)); z may equal x.  `skip`, `live` as for the Krylov kernels;
+// sc: scratch (NULL: the handle's own).
+die_status defl_apply(defl_s* d, const double2* x, double2* z, const int* skip, cudaStream_t st, bool live = false,
+                      const DeflScratch* sc = nullptr);
 // The same entirely in complex64 (copy of V, FP32 sums), for the FP32-inner solves.  With
 // inv != NULL the input is first formed from the FP64 vector w: w *= *inv, x = complex64(w).
 die_status defl_apply32(defl_s* d, float2* x, double2* w, const double* inv, float2* z, const int* skip,
-                        cudaStream_t st, bool live = false);
+                        cudaStream_t st, bool live = false, const DeflScratch* sc = nullptr);
 }  // namespace die

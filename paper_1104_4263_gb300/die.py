@@ -64,6 +64,8 @@ EXPORTS = {
     "dieop_destroy": (None, [ct.c_void_p]),
     "gmres_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p, ct.c_void_p,
                                ct.POINTER(GmresReport), ct.c_void_p]),
+    "gmres_solve_batch": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_int, ct.c_void_p,
+                                     ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "deflation_build": (ct.c_int, [ct.c_void_p, ct.POINTER(DeflOpts), ct.c_void_p, ct.POINTER(ct.c_void_p),
                                    ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
     "deflation_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -280,6 +282,35 @@ class Operator:
         if hist is not None:
             out["history"] = hist[:rep.history_len].copy()
         return x, out
+
+    def solve_batch(self, B, X=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
+                    regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
+                    stream=None, reorth_eta: float = 0.0):
+        """Concurrent restarted GMRES on the right-hand sides B[k] (complex128, shape
+        (nrhs, 2, n2, n1)); returns (X, list of report dicts)."""
+        import torch
+        if B.dtype != torch.complex128 or not B.is_cuda or not B.is_contiguous():
+            raise TypeError("solve_batch takes a contiguous complex128 CUDA tensor")
+        if B.numel() % (2 * self.N) != 0:
+            raise ValueError("B must hold nrhs field vectors of 2 * n1 * n2 values")
+        nrhs = B.numel() // (2 * self.N)
+        use_x0 = X is not None
+        if X is None:
+            X = torch.empty_like(B)
+        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, 0, float(reorth_eta))
+        reps = (GmresReport * nrhs)()
+        d = deflation.handle if deflation is not None else None
+        code = _lib().gmres_solve_batch(self._h, d, ct.byref(opts), nrhs, _ptr(B), _ptr(X),
+                                        ct.cast(reps, ct.c_void_p), _stream(stream))
+        if code not in (0, 5):
+            raise DieError(code, "gmres_solve_batch")
+        outs = []
+        for r in reps:
+            ok = r.rel_res_solved <= tol
+            outs.append({"converged": bool(ok), "cycles": r.cycles, "iters": r.iters, "n_apply": r.n_apply,
+                         "rel_res_solved": r.rel_res_solved, "rel_res_orig": r.rel_res_orig,
+                         "t_total": r.t_total, "n_reorth": r.n_reorth})
+        return X, outs
 
 
 class Deflation:

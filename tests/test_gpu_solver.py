@@ -201,3 +201,24 @@ def test_full_size_solve_residuals(inner):
     assert abs(rep["rel_res_solved"] - r_solved) <= 1e-8 * r_solved
     assert abs(rep["rel_res_orig"] - r_orig) <= 1e-8 * r_orig
     assert r_solved < 0.5
+
+
+@pytest.mark.parametrize("inner", [die.DIE_FP64, die.DIE_FP32_INNER])
+def test_solve_batch_equals_single_solves(inner):
+    """Three incidence angles solved concurrently (gmres_solve_batch): each solution and
+    step count is identical to a single gmres_solve of that right-hand side (regularised,
+    deflated, on the compile-time FFT path and with a ragged general-path grid)."""
+    for n1, n2 in ((128, 128), (40, 33)):
+        p = W.core_shell(max(n1, n2), side=1.5, r_core=0.3, r_shell=0.6, eps_core=2.0 + 0.1j, eps_shell=4.0 + 0.2j)
+        eps = p.eps_r[:n2, :n1].copy()
+        op = die.Operator(eps, p.h)
+        D = die.Deflation(op, 6, tol=1e-4, regularized=True, inner=inner)
+        B = torch.stack([op.plane_wave(psi) for psi in (0.0, 0.7, 2.1)]).contiguous()
+        X, reps = op.solve_batch(B, restart=20, tol=1e-7, max_iters=5000, regularized=True, inner=inner,
+                                 deflation=D)
+        for k in range(3):
+            xk, rk = op.solve(B[k].clone(), restart=20, tol=1e-7, max_iters=5000, regularized=True, inner=inner,
+                              deflation=D)
+            assert reps[k]["iters"] == rk["iters"]
+            assert torch.equal(X[k], xk)
+            assert reps[k]["converged"]
