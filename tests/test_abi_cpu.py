@@ -26,7 +26,7 @@ def lib():
     return die.lib()
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_core_calls():
     names = declared_functions()
     for n in ["dieop_create", "dieop_apply", "dieop_apply_regularized", "gmres_solve", "deflation_build",
               "dieop_destroy", "deflation_destroy", "die_status_str"]:
