@@ -477,6 +477,10 @@ __global__ void __launch_bounds__(kRedThreads) basis_axpy_kernel(const VT* __res
                 r = dec.always || tot < dec.eta2 * dec.before2->x;
                 *dec.reorth = r;
                 *dec.skip2 = (dec.done && *dec.done) || !r;
+                if (r && dec.abort_flags) {          // single-pass cycle: stop it here
+                    *dec.abort_flags |= 8;
+                    *dec.abort_done = 1;
+                }
             }
             if (dec.inv && !r) *dec.inv = inv_norm(tot);
         }
@@ -579,6 +583,10 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
                 r = dec.always || tot < dec.eta2 * dec.before2->x;
                 *dec.reorth = r;
                 *dec.skip2 = (dec.done && *dec.done) || !r;
+                if (r && dec.abort_flags) {          // single-pass cycle: stop it here
+                    *dec.abort_flags |= 8;
+                    *dec.abort_done = 1;
+                }
             }
             const double iv = inv_norm(tot);
             if (dec.inv && !r) *dec.inv = iv;
@@ -817,7 +825,7 @@ static die_status k_update_defl(const double2* V, long ldv, int k, const double2
 
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
                     int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st,
-                    double* inv, const DeflProj* dp, double* VM) {
+                    double* inv, const DeflProj* dp, double* VM, int* abort_flags, int* abort_done) {
     Dgks dec;
     dec.before2 = h1 + nv;
     dec.reorth = reorth;
@@ -826,9 +834,12 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.inv = inv;
     dec.always = eta2 >= 1.0 ? 1 : 0;
     dec.eta2 = eta2;
+    dec.abort_flags = abort_flags;
+    dec.abort_done = abort_done;
     DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true, VM));
     if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true, VM));
     else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true, VM));
+    if (abort_flags) return DIE_OK;   // single-pass cycle: no second-pass launches
     Dgks last;                       // second pass: no decision, only the scale factor
     last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;

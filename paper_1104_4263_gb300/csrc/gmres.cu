@@ -362,6 +362,11 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
         status = DIE_OK;
     }
+    // Cycles start single-pass: the second Gram-Schmidt pass is almost never needed, so
+    // its kernels are not launched; a cycle in which one would have been needed stops and
+    // runs again with the DGKS passes (identical to running it that way from the start),
+    // and the solve keeps them from then on.
+    bool optimistic = eta2 < 1.0;
     while (status == DIE_ENOCONV) {
         // r = btilde - Atilde x in FP64 into V_0
         if (cycles == 0 && !o->use_x0) {
@@ -378,6 +383,8 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         if (rel <= o->tol) { status = DIE_OK; break; }
         if (iters >= o->max_iters) break;
         DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32, Vm));
+        int hk[8];
+        for (;;) {   // one cycle; a single-pass cycle that met a needed second pass runs again
         if (fold)   // cf for v_0
             DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, c->ds.s, defl->M32, c->ds.c32,
                              c->ds.rs, nullptr, st));
@@ -429,7 +436,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 2], st));
             DIE_TRY(cgs_dgks(V, ldv, j + 1, w, n, S.h1 + (long)j * (m + 3), S.h2 + (long)j * (m + 3), S.nrm + 2 * j,
                              S.reorth + j, S.skip2, S.done, eta2, c->rs, st, S.inv + j, fold ? &dp : nullptr,
-                             Vm));
+                             Vm, optimistic ? S.flags : nullptr, optimistic ? S.done : nullptr));
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
             DIE_CUDA_TRY(cudaEventRecord(c->fork, st));
             DIE_CUDA_TRY(cudaStreamWaitEvent(side, c->fork, 0));
@@ -437,10 +444,15 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         }
         DIE_CUDA_TRY(cudaEventRecord(c->back, side));
         DIE_CUDA_TRY(cudaStreamWaitEvent(st, c->back, 0));
-        int hk[8];
         DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(hk, c->host, sizeof hk);
+        if (optimistic && (hk[2] & 8)) {   // v_0 and the residual are intact: rerun with DGKS passes
+            optimistic = false;
+            continue;
+        }
+        break;
+        }
         const int k = hk[1], flags = hk[2];
         if (o->timing) {
             for (int j = 0; j < k; j++) {

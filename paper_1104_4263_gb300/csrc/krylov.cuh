@@ -42,6 +42,11 @@ struct Dgks {
     double* inv = nullptr;             // may be NULL
     int always = 0;
     double eta2 = 0.5;
+    // Single-pass (optimistic) cycles: no second pass is launched; when one would be
+    // needed the deciding block sets bit 3 of *abort_flags and *abort_done = 1 (the
+    // cycle is then run again with second passes).  NULL: normal DGKS.
+    int* abort_flags = nullptr;
+    int* abort_done = nullptr;
 };
 
 // Deflation projections folded into a Gram-Schmidt update (FP32-inner deflated solves):
@@ -121,11 +126,13 @@ die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, c
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
 // inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).
 // dp != NULL folds the deflation projections of the final w into the update passes.
+// abort_flags != NULL: single pass only (see Dgks::abort_flags; abort_done = done).
 // VM != NULL: both passes in the three-multiplication form, with m = Re - Im of each basis
 // vector V_i stored in VM (same stride as V) by whatever normalised V_i.
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2,
                     double2* nrm, int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs,
-                    cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr, double* VM = nullptr);
+                    cudaStream_t st, double* inv = nullptr, const DeflProj* dp = nullptr, double* VM = nullptr,
+                    int* abort_flags = nullptr, int* abort_done = nullptr);
 
 // v *= 1 / sqrt(re(*nrm2)) if positive; v *= *inv.  v32 != NULL also receives the
 // scaled vector rounded to complex64.
