@@ -17,8 +17,10 @@ value = regularised DIE products (applications of A_R A) per second over the tim
 steps.  Other keys: the same through the public API with host buffers (e2e); plain
 FP64 GMRES(30) on A for the same step budget; time-to-tolerance against plain FP64 on
 problems that converge (the paper's Section 4 test squares with the Table 2
-fair-memory settings, and the 32^2 cylinder); the bare regularised product rate; the
-roofline of the dominant kernel; the CPU oracle on this machine's cores.
+fair-memory settings, and the 32^2 cylinder); the bare regularised product rate, alone
+and batched over 8 right-hand sides (matvec); 4 incidence angles solved one after another
+and concurrently (batch_solve); the roofline of the dominant kernel; the CPU oracle on
+this machine's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
