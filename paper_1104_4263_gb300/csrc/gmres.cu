@@ -3,21 +3,28 @@
 //
 // One cycle runs entirely on the device without host round trips.  Each Arnoldi
 // vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion: a second
-// pass runs only when the first one left less than eta of ||w|| (eta = 0.01 unless the
-// caller sets it); the device decides, and the second-pass kernels return at once when
-// it is not needed.  The new Hessenberg column is rotated by Givens rotations on the
-// device, on a side stream one step behind, since the next Arnoldi step does not need
-// the rotations; the normalisation of the new vector uses 1 / ||w|| from the last
-// Gram-Schmidt kernel.  When the residual estimate reaches tol the Givens step sets a
-// device flag that makes the kernels of the remaining steps skip their work.  The host
-// reads one flag set per cycle.  Between cycles the residual btilde - Atilde x is
-// recomputed in FP64 (in the FP32-inner form this is the iterative-refinement step).
+// pass only when the first left less than eta of ||w|| (eta = 0.01 unless the caller
+// sets it).  Cycles start single-pass (the second-pass kernels are not launched); a
+// cycle in which the criterion fires stops and runs again with the second passes, and
+// the solve keeps them.  The passes use the three-multiplication form of the complex
+// products (Re - Im of every basis vector is stored when the vector is normalised).
+// The new Hessenberg column is rotated by Givens rotations on the device, on a side
+// stream one step behind, since the next Arnoldi step does not need the rotations; the
+// normalisation of the new vector uses 1 / ||w|| from the last Gram-Schmidt kernel.
+// When the residual estimate reaches tol the Givens step sets a device flag that makes
+// the kernels of the remaining steps skip their work.  The host reads one flag set per
+// cycle.  Between cycles the residual btilde - Atilde x is recomputed in FP64 (in the
+// FP32-inner form this is the iterative-refinement step).
 //
 // FP32-inner form: the products with Atilde inside a cycle run in complex64 and the
 // deflation P^-1 uses a complex64 copy of V and M with FP32 sums (P^-1 is one fixed
 // preconditioner for the whole solve, so its rounding only changes the
 // preconditioner, and the FP64 restart residual corrects the iterate).  Arnoldi,
 // least squares and the restart residual are FP64 in both forms.
+//
+// A solve runs in a context (SolverCache): buffers, streams, deflation scratch and,
+// for the right-hand sides of gmres_solve_batch, a product workspace of its own, so
+// that several solves can run at once on one operator.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
