@@ -373,7 +373,7 @@ def main():
                                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz (FMA probe: 1.255 TFLOP/s)"}
 
     out["matvec"] = matvec_rates(op, p, die, torch)
-    out["batch_solve"] = batch_solve_rates(op, D, die, torch)
+    out["batch_solve"] = [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)]
     if not args.no_compare:
         out["plain_fp64_same_budget"] = plain_fp64(op, b, args.step_iters, dt / args.steps, last)
         out["time_to_tol"] = time_to_tol(die, W, torch)

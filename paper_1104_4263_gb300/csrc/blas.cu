@@ -783,7 +783,7 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
                      V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0, VM));
     } else {
         DIE_PROF(PK_LINCOMB, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
-                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, (double2*)nullptr, d, 0, rs, skip, 0, (const double*)nullptr));
+                     V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, (double2*)nullptr, d, 0, rs, skip, 0, VM));
     }
     DIE_LAUNCH_CHECK();
     return DIE_OK;

@@ -478,11 +478,12 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         if (k == 0) { status = DIE_EBREAKDOWN; break; }
         DIE_TRY(k_gmres_lsq(S, st));
         if (defl) {
-            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, nullptr, c->tmp, n, nullptr, nullptr, c->rs, nullptr, st));
+            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, nullptr, c->tmp, n, nullptr, nullptr, c->rs, nullptr, st, false,
+                                 Vm));
             DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st, false, &c->ds));
             DIE_TRY(k_basis_axpy(c->tmp, ldv, 1, c->one, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
         } else {
-            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
+            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st, false, Vm));
         }
         // a singular triangular factor (breakdown with no exact solution) shows up after the LSQ
         DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -107,6 +107,7 @@ die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, co
                     cudaStream_t st, bool live = false);
 // out = base + sign * sum_i V_i c_i (base may be NULL = 0, out may equal base), c = coef.
 // nrm2 != NULL: ||out||^2 into nrm2[0] (device), and the DGKS decision if dec != NULL.
+// VM != NULL: the three-multiplication form, with Re - Im of every V_i in VM.
 die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, double sign, const double2* base,
                         double2* out, long n, double2* nrm2, const Dgks* dec, const RedScratch& rs,
                         const int* skip, cudaStream_t st, bool live = false, const double* VM = nullptr);
