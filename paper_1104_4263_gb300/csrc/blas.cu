@@ -25,12 +25,6 @@ template <> struct acc_of<float2> { using type = float; };
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return v;
-}
-
 // Warp sums of K = 2^P values per lane by recursive halving: at offset o = 16, 8, ...
 // a lane keeps the half of its current values selected by (lane & o) and adds the
 // partner's copy of that half.  Afterwards lane l holds in v[0 .. C) (C = max(K/32, 1))

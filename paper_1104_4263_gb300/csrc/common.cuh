@@ -32,11 +32,6 @@ template <typename V>
 __host__ __device__ __forceinline__ V cmul(V a, V b) {
     V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
-// conj(a) * b
-template <typename V>
-__host__ __device__ __forceinline__ V cmulc(V a, V b) {
-    V r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
-}
 template <typename V, typename S>
 __host__ __device__ __forceinline__ V cscale(V a, S s) { V r; r.x = a.x * s; r.y = a.y * s; return r; }
 // a * (-i) and a * (+i)

@@ -73,3 +73,11 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert out.value is None
     assert lib.gmres_solve(None, None, None, None, None, None, None) == 1
     assert lib.dieop_apply(None, None, None, None) == 1
+    assert lib.dieop_apply_batch(None, 1, None, None, 0, None) == 1
+    assert lib.gmres_solve_batch(None, None, None, 1, None, None, None, None) == 1
+    opts = die.GmresOpts(30, 100, 1e-6, 0, 0, 0, 0, 0.0)
+    dummy = ct.c_void_p(1)                       # never dereferenced: the checks below return first
+    for nrhs in (0, 17):                          # outside [1, 16]
+        assert lib.gmres_solve_batch(dummy, None, ct.byref(opts), nrhs, dummy, dummy, None, None) == 1
+    for nrhs in (0, 1025):                        # outside [1, 1024]
+        assert lib.dieop_apply_batch(dummy, nrhs, dummy, dummy, 1, None) == 1
