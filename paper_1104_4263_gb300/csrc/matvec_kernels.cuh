@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
 // First row pass of a deflated FP32-inner product (complex64): per element
 // z = v + sum_i V32_i cf_i (v = w / ||w|| written back to the FP64 Arnoldi vector, or
 // the complex64 x), stored to zout for the later passes, then chi * z and the forward
-// row transform as in k1_fast.  The basis loads go four vectors (32 loads) at a time.
+// row transform as in k1_fast.  The basis loads go five vectors (40 loads) at a time.
 template <int L>
 __global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, const float2* __restrict__ chi,
                                                     float2* __restrict__ zout, float2* __restrict__ W,
@@ -445,17 +445,18 @@ __global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, c
             for (int e = 0, q = 0; e < 16; e++)
                 if (F0::index(e) < n1) zq[q++] = d.x[off + F0::index(e)];
         }
-        for (int i0 = 0; i0 < d.r; i0 += 4) {
-            C a[4][8];
+        constexpr int VB = 5;                     // basis vectors per round of loads (40 in flight)
+        for (int i0 = 0; i0 < d.r; i0 += VB) {
+            C a[VB][8];
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < VB; v++) {
                 const C* p = d.V32 + (long)(i0 + v < d.r ? i0 + v : i0) * d.ld + off;
 #pragma unroll
                 for (int e = 0, q = 0; e < 16; e++)
                     if (F0::index(e) < n1) a[v][q++] = p[F0::index(e)];
             }
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < VB; v++) {
                 if (i0 + v < d.r) {
                     const C cv = cs[i0 + v];
 #pragma unroll
