@@ -34,19 +34,19 @@ struct FftPlan {
 
 // ------------------------------------------------------------------ small DFTs
 template <typename V, bool INV>
-__device__ __forceinline__ V rot_q(V a) { return INV ? mul_pi(a) : mul_mi(a); }   // * (-+ i)
+__host__ __device__ __forceinline__ V rot_q(V a) { return INV ? mul_pi(a) : mul_mi(a); }   // * (-+ i)
 
 template <typename V, bool INV>
-__device__ __forceinline__ void dft2(V& a, V& b) { V t = a; a = cadd(t, b); b = csub(t, b); }
+__host__ __device__ __forceinline__ void dft2(V& a, V& b) { V t = a; a = cadd(t, b); b = csub(t, b); }
 
 template <typename V, bool INV>
-__device__ __forceinline__ void dft4(V& x0, V& x1, V& x2, V& x3) {
+__host__ __device__ __forceinline__ void dft4(V& x0, V& x1, V& x2, V& x3) {
     V a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = rot_q<V, INV>(csub(x1, x3));
     x0 = cadd(a, c); x2 = csub(a, c); x1 = cadd(b, d); x3 = csub(b, d);
 }
 
 template <typename V, bool INV>
-__device__ __forceinline__ void dft3(V& x0, V& x1, V& x2) {
+__host__ __device__ __forceinline__ void dft3(V& x0, V& x1, V& x2) {
     using T = typename real_of<V>::type;
     const T h3 = (T)0.86602540378443864676;   // sqrt(3)/2
     V s = cadd(x1, x2), d = csub(x1, x2);
@@ -57,7 +57,7 @@ __device__ __forceinline__ void dft3(V& x0, V& x1, V& x2) {
 
 // multiply by exp(-+ i pi q / 4), q = 1..3
 template <typename V, bool INV>
-__device__ __forceinline__ V w8(V a, int q) {
+__host__ __device__ __forceinline__ V w8(V a, int q) {
     using T = typename real_of<V>::type;
     const T r2 = (T)0.70710678118654752440;
     if (q == 1) { V t = INV ? mk((T)(a.x - a.y), (T)(a.x + a.y)) : mk((T)(a.x + a.y), (T)(a.y - a.x)); return cscale(t, r2); }
@@ -68,7 +68,7 @@ __device__ __forceinline__ V w8(V a, int q) {
 }
 
 template <typename V, bool INV>
-__device__ __forceinline__ void dft8(V* x) {
+__host__ __device__ __forceinline__ void dft8(V* x) {
     // even/odd split: E = DFT4(x0,x2,x4,x6), O = DFT4(x1,x3,x5,x7); y_s = E_s + w8^s O_s
     V e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
     V o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
@@ -82,7 +82,7 @@ __device__ __forceinline__ void dft8(V* x) {
 }
 
 template <typename V, bool INV>
-__device__ __forceinline__ void dft16(V* x) {
+__host__ __device__ __forceinline__ void dft16(V* x) {
     using T = typename real_of<V>::type;
     // cos / sin of s pi / 8, s = 0..7
     const T c[8] = {(T)1.0, (T)0.92387953251128675613, (T)0.70710678118654752440, (T)0.38268343236508977173,
@@ -104,7 +104,8 @@ __device__ __forceinline__ void dft16(V* x) {
 }
 
 template <typename V, int R, bool INV>
-__device__ __forceinline__ void dft(V* x) {
+__host__ __device__ __forceinline__ void dft(V* x) {
+    static_assert(R == 2 || R == 3 || R == 4 || R == 8 || R == 16, "radix 2, 3, 4, 8 or 16");
     if constexpr (R == 2) dft2<V, INV>(x[0], x[1]);
     else if constexpr (R == 3) dft3<V, INV>(x[0], x[1], x[2]);
     else if constexpr (R == 4) dft4<V, INV>(x[0], x[1], x[2], x[3]);

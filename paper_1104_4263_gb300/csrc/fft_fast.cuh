@@ -9,8 +9,8 @@
 //    P(base) + c + (c >> 4): one base pointer per stage, immediate offsets after it.
 //    (Loads: base = t, c = b G + r L / R, a multiple of 16.  Stores: base =
 //    (t - t mod Ns) R + t mod Ns with c = b G R + s Ns, or base = t with
-//    c = b G + s Ns in the last stage.  The bound on the low bits holds for every
-//    plan of pow2_plan with L >= 256.)
+//    c = b G + s Ns in the last stage.  The bound on the low bits is checked at compile
+//    time for every stage of every instantiated plan.)
 //  * While Ns divides G (every stage but possibly the last), the twiddle index
 //    k = (t + b G) mod Ns is the same for all butterflies of a thread, so the R - 1
 //    twiddles are loaded once per stage.
@@ -28,15 +28,45 @@ template <int L> struct P2 {
 };
 
 
+// Twiddle load: read-only cache path on the device, plain load on the host (the stage
+// code also runs on the host, where a CPU test checks it against a plain DFT).
+template <typename V> __host__ __device__ __forceinline__ V ld_tw(const V* p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// (base mod 16) + (c mod 16) < 16 for every load and store of a stage (see the top of
+// the file).
+template <int L, int R, int NS>
+constexpr bool padding_linear() {
+    constexpr int G = L / 16, B = 16 / R, LR = L / R;
+    constexpr bool uniform = (G % NS) == 0;
+    for (int t = 0; t < G; t++) {
+        const int sb = uniform ? (t & ~(NS - 1)) * R + (t & (NS - 1)) : t;
+        for (int b = 0; b < B; b++)
+            for (int r = 0; r < R; r++) {
+                const int cl = b * G + r * LR;
+                const int cs = (uniform ? b * G * R : b * G) + r * NS;
+                if ((t & 15) + (cl & 15) >= 16) return false;
+                if ((sb & 15) + (cs & 15) >= 16) return false;
+            }
+    }
+    return true;
+}
+
 template <typename V, int L, int R, int NS, bool INV>
 struct FStage {
     static constexpr int kR = R;
     static constexpr int G = L / 16, B = 16 / R, LR = L / R;
     static constexpr bool kUniformK = (G % NS) == 0;    // twiddle index shared by the thread's butterflies
     static_assert(kUniformK || B * G <= NS, "last-stage layout");
+    static_assert(padding_linear<L, R, NS>(), "shared-memory padding is not linear over this stage's accesses");
 
     // x[b R + r] = buf[P(t + b G + r L / R)]
-    __device__ static __forceinline__ void load(const V* __restrict__ buf, V (&x)[16], int t) {
+    __host__ __device__ static __forceinline__ void load(const V* __restrict__ buf, V (&x)[16], int t) {
         const V* p = buf + pidx(t);
 #pragma unroll
         for (int b = 0; b < B; b++)
@@ -48,7 +78,7 @@ struct FStage {
     }
 
     // twiddles, then the radix-R DFTs
-    __device__ static __forceinline__ void compute(V (&x)[16], int t, const V* __restrict__ tw) {
+    __host__ __device__ static __forceinline__ void compute(V (&x)[16], int t, const V* __restrict__ tw) {
         if constexpr (NS > 1) {
             constexpr int step = L / (NS * R);     // tw[step * r * k] = exp(-2 pi i r k / (NS R))
             if constexpr (kUniformK) {
@@ -56,7 +86,7 @@ struct FStage {
                 V w[R];
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    w[r] = __ldg(&tw[step * r * k]);
+                    w[r] = ld_tw(&tw[step * r * k]);
                     if (INV) w[r].y = -w[r].y;
                 }
 #pragma unroll
@@ -69,7 +99,7 @@ struct FStage {
                     const int k = t + b * G;
 #pragma unroll
                     for (int r = 1; r < R; r++) {
-                        V w = __ldg(&tw[step * r * k]);
+                        V w = ld_tw(&tw[step * r * k]);
                         if (INV) w.y = -w.y;
                         x[b * R + r] = cmul(x[b * R + r], w);
                     }
@@ -81,7 +111,7 @@ struct FStage {
     }
 
     // buf[P(out)] = x, out = (j - k) R + k + s NS for butterfly j = t + b G, k = j mod NS
-    __device__ static __forceinline__ void store(V* __restrict__ buf, const V (&x)[16], int t) {
+    __host__ __device__ static __forceinline__ void store(V* __restrict__ buf, const V (&x)[16], int t) {
         const int base = kUniformK ? (t & ~(NS - 1)) * R + (t & (NS - 1)) : t;
         V* p = buf + pidx(base);
 #pragma unroll
@@ -95,14 +125,14 @@ struct FStage {
 
     // The same stage on two independent transforms (x0, x1) at the same indices, with the
     // twiddles loaded once for both.
-    __device__ static __forceinline__ void compute2(V (&x0)[16], V (&x1)[16], int t, const V* __restrict__ tw) {
+    __host__ __device__ static __forceinline__ void compute2(V (&x0)[16], V (&x1)[16], int t, const V* __restrict__ tw) {
         if constexpr (NS > 1) {
             constexpr int step = L / (NS * R);
             if constexpr (kUniformK) {
                 const int k = t & (NS - 1);
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    V w = __ldg(&tw[step * r * k]);
+                    V w = ld_tw(&tw[step * r * k]);
                     if (INV) w.y = -w.y;
 #pragma unroll
                     for (int b = 0; b < B; b++) {
@@ -116,7 +146,7 @@ struct FStage {
                     const int k = t + b * G;
 #pragma unroll
                     for (int r = 1; r < R; r++) {
-                        V w = __ldg(&tw[step * r * k]);
+                        V w = ld_tw(&tw[step * r * k]);
                         if (INV) w.y = -w.y;
                         x0[b * R + r] = cmul(x0[b * R + r], w);
                         x1[b * R + r] = cmul(x1[b * R + r], w);

@@ -1,0 +1,91 @@
+// Host run of the compile-time Stockham stages of the product kernels (fft_fast.cuh):
+// every thread of a transform group executes its stage loads, twiddles, radix-R DFTs and
+// stores in turn, with the block barriers between stages taken as phase boundaries.  The
+// result is compared with the plain DFT sum in long double.  Prints one line per
+// (length, direction, precision): "L dir prec max_rel_err".
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <vector>
+
+#include "../paper_1104_4263_gb300/csrc/fft_fast.cuh"
+
+using namespace die;
+
+template <typename V, int L, bool INV, int S, int NS>
+void run_stages(V* buf, std::vector<std::array<V, 16>>& x, const V* tw) {
+    if constexpr (S < NS) {
+        using St = typename PlanStage<V, L, INV, S>::St;
+        constexpr int G = L / 16;
+        using Regs = V[16];
+        if constexpr (S > 0)
+            for (int t = 0; t < G; t++) St::load(buf, *reinterpret_cast<Regs*>(x[t].data()), t);
+        for (int t = 0; t < G; t++) St::compute(*reinterpret_cast<Regs*>(x[t].data()), t, tw);
+        if constexpr (S + 1 < NS)
+            for (int t = 0; t < G; t++) St::store(buf, *reinterpret_cast<const Regs*>(x[t].data()), t);
+        run_stages<V, L, INV, S + 1, NS>(buf, x, tw);
+    }
+}
+
+template <typename V, int L, bool INV>
+double max_rel_err() {
+    using T = typename real_of<V>::type;
+    constexpr int G = L / 16;
+    constexpr FftPlan pl = INV ? P2<L>::inv : P2<L>::fwd;
+    using F0 = typename PlanStage<V, L, INV, 0>::St;
+    using FL = typename PlanStage<V, L, INV, pl.ns - 1>::St;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<V> tw(L), buf(padded_len(L));
+    for (int m = 0; m < L; m++) {
+        const long double a = -2.0L * pi * m / L;
+        tw[m] = mk((T)std::cos(a), (T)std::sin(a));
+    }
+    std::vector<std::complex<long double>> in(L);
+    unsigned s = 20110421u;                       // fixed LCG: the input needs no other source
+    for (int i = 0; i < L; i++) {
+        s = s * 1103515245u + 12345u;
+        const double a = (s >> 8) / 16777216.0 - 0.5;
+        s = s * 1103515245u + 12345u;
+        const double b = (s >> 8) / 16777216.0 - 0.5;
+        in[i] = {(long double)(T)a, (long double)(T)b};
+    }
+    std::vector<std::array<V, 16>> x(G);
+    for (int t = 0; t < G; t++)
+        for (int e = 0; e < 16; e++) {
+            const auto v = in[t + F0::index(e)];
+            x[t][e] = mk((T)v.real(), (T)v.imag());
+        }
+    run_stages<V, L, INV, 0, pl.ns>(buf.data(), x, tw.data());
+    long double err = 0, nrm = 0;
+    for (int t = 0; t < G; t++)
+        for (int e = 0; e < 16; e++) {
+            const int k = t + FL::index(e);
+            std::complex<long double> acc = 0;
+            for (int j = 0; j < L; j++) {
+                const long double a = (INV ? 2.0L : -2.0L) * pi * (long double)((long)j * k % L) / L;
+                acc += in[j] * std::complex<long double>(std::cos(a), std::sin(a));
+            }
+            const std::complex<long double> got(x[t][e].x, x[t][e].y);
+            err = std::max(err, std::abs(got - acc));
+            nrm = std::max(nrm, std::abs(acc));
+        }
+    return (double)(err / nrm);
+}
+
+template <int L> void report() {
+    std::printf("%d fwd f64 %.3e\n", L, max_rel_err<double2, L, false>());
+    std::printf("%d inv f64 %.3e\n", L, max_rel_err<double2, L, true>());
+    std::printf("%d fwd f32 %.3e\n", L, max_rel_err<float2, L, false>());
+    std::printf("%d inv f32 %.3e\n", L, max_rel_err<float2, L, true>());
+}
+
+int main() {
+    report<256>();
+    report<512>();
+    report<1024>();
+    report<2048>();
+    report<4096>();
+    return 0;
+}
