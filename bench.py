@@ -50,6 +50,11 @@ WORKLOAD = ("core-shell 512x512 (eps -2+0.1i core R1.5, 20+0.5i shell R2.5, side
             "FP32 products + FP64 Krylov, 1500 Arnoldi steps per step")
 L2_NOTE = "working set > L2 (Krylov basis 31 x 8.4 MB, deflation basis 20 x 4.2 MB)"
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12    # 152 SMs x 2 DFMA/clk x 2.07 GHz; a probe measured 1.255
+# ncu DRAM bytes (read + write) of one launch of the FP64 projection kernel on this
+# workload: 16 basis vectors with their Re - Im planes, and the norm of w, over
+# 2N = 524288 (profiles/dots_fp64_core_shell_512.md).  Its traffic grows with the
+# vectors read, so it is scaled to the bench's average launch by the algorithmic bytes.
+NCU_DOTS = {"dram_bytes": 213.669888e6 + 3.034880e6, "nv": 16, "n": 524288}
 
 
 def dist_env():
@@ -202,6 +207,11 @@ def work_model(cls, p, op, r, steps_per_cycle, cycles, products, fp64_products):
     if cls == "defl_update":                # FP64 P^-1 in the update of x, once per cycle
         return "hbm", cycles * (r * n * 16 + 2 * n * 16)
     m = steps_per_cycle
+    if cls == "dots_bytes":
+        # step j: j+1 basis vectors (16 B) and their Re - Im planes (8 B), w read once;
+        # per cycle the residual norm and the FP64 deflation projections (r vectors + x)
+        per_cycle = sum((j + 1) * 24 + 16 for j in range(m)) + 16 + 16 * r + 16
+        return "hbm", cycles * per_cycle * n + 16 * n
     if cls == "dots":
         # step j of a cycle: j+1 projections + the norm of w; per cycle one norm of the
         # residual, one FP64 deflation projection set (r) for the update of x
@@ -371,6 +381,14 @@ def main():
                                "unit": "TFLOP/s", "frac": (per_launch / avg_s / 1e12) / FP64_PEAK_TFLOPS,
                                "traffic": None, "kernel": best, "algorithmic_flops_per_launch": per_launch,
                                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz (FMA probe: 1.255 TFLOP/s)"}
+            if best == "dots" and 2 * p.N == NCU_DOTS["n"]:
+                _, tot_bytes = work_model("dots_bytes", p, op, D.r, RESTART, cycles, prof_products, fp64_products)
+                alg_bytes = tot_bytes / k["launches"]
+                captured_alg = (NCU_DOTS["nv"] * 24 + 16) * NCU_DOTS["n"]
+                out["roofline"]["traffic"] = NCU_DOTS["dram_bytes"] * alg_bytes / captured_alg
+                out["roofline"]["algorithmic_bytes_per_launch"] = alg_bytes
+                out["roofline"]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16-vector "
+                                                     "launch, scaled to the average launch by the algorithmic bytes")
 
     out["matvec"] = matvec_rates(op, p, die, torch)
     out["batch_solve"] = [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)]
