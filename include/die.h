@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define DIE_ABI_VERSION 1
+#define DIE_ABI_VERSION 2
 
 typedef enum die_status {
     DIE_OK = 0,
@@ -139,6 +139,12 @@ typedef struct gmres_opts {
                               <= 0 selects 0.01 (one CGS pass loses about eps ||w||/||w'|| of
                               orthogonality: <= 2.3e-14 at 0.01); 1/sqrt(2) is the classical
                               choice; >= 1 always re-orthogonalises                             */
+    int graph;             /* 1: the Arnoldi steps of a cycle run as one CUDA graph launch.  A
+                              configuration (operator context, deflation handle, options, cycle
+                              length) is captured the first time it recurs after one direct run
+                              and kept by the context (up to 4) for later cycles and solves;
+                              results are bit-identical to graph = 0.  Ignored (no graph) when
+                              timing = 1 or kernel timing (die_prof_*) is on                   */
 } gmres_opts;
 
 typedef struct gmres_report {
@@ -152,6 +158,7 @@ typedef struct gmres_report {
     int history_cap;       /* its length                                                       */
     int history_len;       /* entries written                                                  */
     int n_reorth;          /* Arnoldi steps that needed the second Gram-Schmidt pass           */
+    int graph_cycles;      /* cycles whose Arnoldi steps ran as a graph launch                 */
 } gmres_report;
 
 /* b, x: device complex128, 2*n1*n2.  defl may be NULL.  report may be NULL.
@@ -244,6 +251,11 @@ die_status die_prof_read(int id, long long* launches, double* total_ms);
 
 /* Human-readable name of a status code (static storage). */
 const char* die_status_str(die_status s);
+
+/* sizeof of the public structures, for bindings that mirror them: sizes[0..n) receives
+ * dieop_desc, gmres_opts, gmres_report, defl_opts (in this order; n <= 4).  DIE_EINVAL
+ * if sizes is NULL or n is outside [1, 4]. */
+die_status die_abi_sizes(long long* sizes, int n);
 
 /* Library ABI version (DIE_ABI_VERSION) for binding checks. */
 int die_abi_version(void);

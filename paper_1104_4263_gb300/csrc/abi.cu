@@ -83,6 +83,7 @@ static void twiddles(int L, std::vector<double2>& d, std::vector<float2>& f) {
 }
 
 static std::atomic<uint64_t> g_next_id{1};
+uint64_t next_handle_id() { return g_next_id.fetch_add(1); }
 
 }  // namespace die
 
@@ -107,6 +108,14 @@ static die_status dmalloc(P** p, size_t bytes) {
 extern "C" {
 
 int die_abi_version(void) { return DIE_ABI_VERSION; }
+
+die_status die_abi_sizes(long long* sizes, int n) {
+    if (!sizes || n < 1 || n > 4) return DIE_EINVAL;
+    const long long all[4] = {(long long)sizeof(dieop_desc), (long long)sizeof(gmres_opts),
+                              (long long)sizeof(gmres_report), (long long)sizeof(defl_opts)};
+    for (int i = 0; i < n; i++) sizes[i] = all[i];
+    return DIE_OK;
+}
 
 const char* die_status_str(die_status s) {
     switch (s) {
@@ -189,7 +198,7 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     cudaFree(scratch);
     if (s != DIE_OK) return s;
     if (flag) return DIE_ESINGULAR;
-    op->id = g_next_id.fetch_add(1);
+    op->id = next_handle_id();
     return DIE_OK;
 }
 

@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
 // The column, the stored rotations and g_j are staged in shared memory by the whole
 // block (one global round trip instead of one per rotation), then thread 0 computes.
 // Everything it reads belongs to step j (its own slots of h1, h2, nrm and reorth).
-__global__ void arnoldi_finish_kernel(GmresDev S, int j, int step) {
+__global__ void arnoldi_finish_kernel(GmresDev S, int j) {
     __shared__ double2 col[kMaxBasis + 2], csv[kMaxBasis], snv[kMaxBasis];
     if (*S.done) return;
     const int ld = S.m + 1;
@@ -656,7 +656,8 @@ __global__ void arnoldi_finish_kernel(GmresDev S, int j, int step) {
     const double2 gj = S.g[j];
     S.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
     S.g[j] = make_double2(c * gj.x, c * gj.y);
-    const double est = hypot(S.g[j + 1].x, S.g[j + 1].y) / S.bnorm;
+    const double est = hypot(S.g[j + 1].x, S.g[j + 1].y) / *S.bnorm;
+    const int step = *S.step0 + j;
     if (step < S.hist_cap) S.hist[step] = est;
     *S.k = j + 1;
     const bool bad = !isfinite(est) || !isfinite(hn);
@@ -728,6 +729,12 @@ __global__ void gmres_lsq_kernel(GmresDev S) {
         if (threadIdx.x == 0) S.y[i] = yi;
         __syncthreads();
     }
+}
+
+__global__ void cycle_scalars_kernel(GmresDev S, double bnorm, int step0) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *S.step0 = step0;
+    *S.bnorm = bnorm;
 }
 
 // Start a cycle: g = (beta, 0, ...), counters cleared; beta = sqrt(re(*beta2)).
@@ -869,8 +876,13 @@ die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st) {
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
-die_status k_arnoldi_finish(GmresDev S, int j, int step, cudaStream_t st) {
-    DIE_PROF(PK_GIVENS, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j, step));
+die_status k_arnoldi_finish(GmresDev S, int j, cudaStream_t st) {
+    DIE_PROF(PK_GIVENS, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j));
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+die_status k_cycle_scalars(GmresDev S, double bnorm, int step0, cudaStream_t st) {
+    DIE_PROF(PK_SMALL, st, cycle_scalars_kernel<<<1, 32, 0, st>>>(S, bnorm, step0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -254,6 +254,7 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     d->n = n;
     d->regularized = reg ? 1 : 0;
     d->op_id = op->id;
+    d->id = next_handle_id();
     DIE_TRY(dalloc((void**)&d->V, (size_t)r * n * sizeof(double2)));
     DIE_TRY(dalloc((void**)&d->M, (size_t)r * r * sizeof(double2)));
     DIE_TRY(dalloc((void**)&d->s, (size_t)(r + 2) * sizeof(double2)));

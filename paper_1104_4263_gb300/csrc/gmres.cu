@@ -33,6 +33,7 @@
 #include <thread>
 #include <vector>
 
+#include "prof.cuh"
 #include "solver.cuh"
 
 namespace die {
@@ -74,6 +75,8 @@ static void free_cache(SolverCache* c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : {c->join[0], c->join[1], c->fork, c->back})
         if (e) cudaEventDestroy(e);
+    for (CycleGraph& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->side) cudaStreamDestroy(c->side);
     delete c;
@@ -267,6 +270,50 @@ static int hist_cap_of(const gmres_opts* o) {
 
 // One solve in context c (its buffers, streams, deflation scratch and, for a batch
 // context, its product workspace); pin: use the L2 window for the deflation basis.
+// Captured cycles.  A context records the configurations (CycleKey) of the cycles it
+// runs; a graph is captured only for a configuration that has already run directly, so
+// every kernel of the cycle has been launched once (first-use attribute calls stay out of
+// the capture).
+static CycleGraph* find_cycle(SolverCache* c, const CycleKey& key) {
+    for (CycleGraph& g : c->graphs)
+        if (g.used && g.key == key) return &g;
+    return nullptr;
+}
+
+static void note_cycle(SolverCache* c, const CycleKey& key) {
+    CycleGraph& slot = c->graphs[c->next_graph];
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    slot.exec = nullptr;
+    slot.key = key;
+    slot.used = true;
+    c->next_graph = (c->next_graph + 1) % kCycleGraphs;
+}
+
+// Captures `steps` from `st` (with the side stream they fork to and join back from) into
+// g->exec.
+template <typename F>
+static die_status capture_cycle(CycleGraph* g, cudaStream_t st, F&& steps) {
+    DIE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const die_status s = steps();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != DIE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (s != DIE_OK) return s;
+        set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        return DIE_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        set_last_cuda_error(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+        return DIE_ECUDA;
+    }
+    g->exec = exec;
+    return DIE_OK;
+}
+
 static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, const void* b_, void* x_,
                             gmres_report* rep, cudaStream_t ust, SolverCache* c, bool pin) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -306,13 +353,15 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
     S.y = sm; sm += m + 3;
     S.nrm = sm; sm += 2 * m;
     S.inv = reinterpret_cast<double*>(sm); sm += m;
-    double2* scal = sm;            // scalars: [0] residual norm^2
+    double2* scal = sm;            // scalars: [0] residual norm^2, [1].x ||btilde||
+    S.bnorm = &scal[1].x;
     S.hist = c->hist;
     S.done = c->ints;
     S.k = c->ints + 1;
     S.flags = c->ints + 2;
     S.skip2 = c->ints + 3;
     S.nreorth = c->ints + 4;
+    S.step0 = c->ints + 5;
     S.reorth = c->ints + 8;
     S.m = m;
     S.jmax = m;
@@ -333,10 +382,12 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
     const double bnorm = sqrt(bn2);
     if (!isfinite(bnorm)) return DIE_ENAN;
     if (!o->use_x0) DIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
-    S.bnorm = bnorm > 0 ? bnorm : 1.0;
+    const double bnorm_ref = bnorm > 0 ? bnorm : 1.0;
 
     die_status status = DIE_ENOCONV;
-    int iters = 0, cycles = 0, hist_len = 0;
+    int iters = 0, cycles = 0, hist_len = 0, graph_cycles = 0;
+    // per-launch event timing cannot be captured into a graph
+    const bool use_graph = o->graph && !o->timing && !g_prof_on;
     double rel = 0, t_mv = 0, t_orth = 0, t_defl = 0;
     const long ldv = n;
     double2* V = c->V;
@@ -391,13 +442,16 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         if (iters >= o->max_iters) break;
         DIE_TRY(k_scale_inv_sqrt(V, n, scal, nullptr, st, v32, Vm));
         int hk[8];
+        const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
+        S.jmax = jmax;
+        DIE_TRY(k_cycle_scalars(S, bnorm_ref, iters, st));
         for (;;) {   // one cycle; a single-pass cycle that met a needed second pass runs again
+        // The Arnoldi steps of the cycle: launched directly, or captured once as a graph.
+        auto steps = [&]() -> die_status {
         if (fold)   // cf for v_0
             DIE_TRY(k_dots32(defl->V32, n, defl->r, c->v32, nullptr, nullptr, n, c->ds.s, defl->M32, c->ds.c32,
                              c->ds.rs, nullptr, st));
         DIE_TRY(k_gmres_init(S, scal, st));
-        const int jmax = m < o->max_iters - iters ? m : o->max_iters - iters;
-        S.jmax = jmax;
         // Step j: v_j = w_{j-1} / ||w_{j-1}|| (j > 0), w = Atilde P^-1 v_j, Gram-Schmidt
         // against v_0..v_j on this stream; the Givens step of j then runs on the side
         // stream while step j+1 starts.  The done flag it sets is read by the kernels
@@ -447,10 +501,33 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
             if (o->timing) DIE_CUDA_TRY(cudaEventRecord(c->ev[4 * j + 3], st));
             DIE_CUDA_TRY(cudaEventRecord(c->fork, st));
             DIE_CUDA_TRY(cudaStreamWaitEvent(side, c->fork, 0));
-            DIE_TRY(k_arnoldi_finish(S, j, iters + j, side));
+            DIE_TRY(k_arnoldi_finish(S, j, side));
         }
         DIE_CUDA_TRY(cudaEventRecord(c->back, side));
         DIE_CUDA_TRY(cudaStreamWaitEvent(st, c->back, 0));
+        return DIE_OK;
+        };
+        CycleKey key;
+        key.defl = defl ? defl->id : 0;
+        key.jmax = jmax;
+        key.m = m;
+        key.optimistic = optimistic ? 1 : 0;
+        key.reg = reg ? 1 : 0;
+        key.mixed = mixed ? 1 : 0;
+        key.fold = fold ? 1 : 0;
+        key.fold_product = fold_product ? 1 : 0;
+        key.vm = Vm ? 1 : 0;
+        key.tol = o->tol;
+        key.eta2 = eta2;
+        CycleGraph* g = find_cycle(c, key);
+        if (use_graph && g) {
+            if (!g->exec) DIE_TRY(capture_cycle(g, st, steps));
+            DIE_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+            graph_cycles++;
+        } else {
+            DIE_TRY(steps());
+            if (!g) note_cycle(c, key);
+        }
         DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(hk, c->host, sizeof hk);
@@ -516,6 +593,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         rep->t_total = seconds_since(t0);
         rep->history_len = 0;
         rep->n_reorth = nre;
+        rep->graph_cycles = graph_cycles;
         if (rep->history && rep->history_cap > 0 && hist_len > 0) {
             const int cnt = hist_len < rep->history_cap ? hist_len : rep->history_cap;
             DIE_CUDA_TRY(cudaMemcpy(rep->history, c->hist, cnt * sizeof(double), cudaMemcpyDeviceToHost));

@@ -84,7 +84,9 @@ struct GmresDev {
     int* reorth;       // m: 1 if the second Gram-Schmidt pass ran at step j
     int* skip2;        // done || !reorth of the current step
     int* nreorth;      // second passes run (counter over the solve)
-    double bnorm, tol;
+    int* step0;        // global index of the cycle's first step: step j's history slot is *step0 + j
+    double* bnorm;     // ||btilde|| (the residual estimates are relative to it)
+    double tol;
     int m, jmax, hist_cap;
 };
 
@@ -149,7 +151,10 @@ die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st);
 
 // GMRES step j after Gram-Schmidt: H(:, j) = h1 (+ h2), H(j+1, j) = ||w||, Givens.
 // Reads only step j's slots, so it may run on a side stream behind the next step.
-die_status k_arnoldi_finish(GmresDev S, int j, int step, cudaStream_t st);
+die_status k_arnoldi_finish(GmresDev S, int j, cudaStream_t st);
+// The per-cycle scalars the cycle's kernels read from device memory (so that a captured
+// cycle replays unchanged): *S.step0 = step0, *S.bnorm = bnorm.
+die_status k_cycle_scalars(GmresDev S, double bnorm, int step0, cudaStream_t st);
 // Solve the k x k upper-triangular R y = g of the current cycle (k read from S.k).
 die_status k_gmres_lsq(GmresDev S, cudaStream_t st);
 die_status k_gmres_init(GmresDev S, const double2* beta2, cudaStream_t st);

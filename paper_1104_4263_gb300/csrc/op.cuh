@@ -49,6 +49,7 @@ struct dieop_s {
 };
 
 namespace die {
+uint64_t next_handle_id();   // process-wide unique identities of operator and deflation handles
 
 OpDev<double> view_d(const dieop_s* op);
 OpDev<float> view_f(const dieop_s* op);

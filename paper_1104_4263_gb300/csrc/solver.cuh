@@ -21,6 +21,24 @@ constexpr int kMaxBatchSolve = 16;   // right-hand sides of one gmres_solve_batc
 
 // Device buffers reused across gmres_solve calls on one operator (one context), or by one
 // right-hand side of gmres_solve_batch (a batch context, with its own product workspace).
+// What a captured cycle (gmres_opts.graph) depends on besides the context's own buffers.
+struct CycleKey {
+    uint64_t defl = 0;          // deflation handle identity (0: none)
+    int jmax = 0, m = 0, optimistic = 0, reg = 0, mixed = 0, fold = 0, fold_product = 0, vm = 0;
+    double tol = 0, eta2 = 0;
+    bool operator==(const CycleKey& o) const {
+        return defl == o.defl && jmax == o.jmax && m == o.m && optimistic == o.optimistic && reg == o.reg &&
+               mixed == o.mixed && fold == o.fold && fold_product == o.fold_product && vm == o.vm &&
+               tol == o.tol && eta2 == o.eta2;
+    }
+};
+struct CycleGraph {
+    bool used = false;              // key holds a configuration this context has run
+    CycleKey key;
+    cudaGraphExec_t exec = nullptr; // its captured cycle, once one has been captured
+};
+constexpr int kCycleGraphs = 4;
+
 struct SolverCache {
     int m_cap = 0;          // Krylov dimension the buffers hold
     long n = 0;             // vector length 2N
@@ -45,6 +63,8 @@ struct SolverCache {
     cudaEvent_t fork = nullptr, back = nullptr;   // stream -> side, side -> stream
     DeflScratch ds;                 // deflation scratch (kMaxBasis + 2 projections)
     Workspace ws;                   // batch contexts: own product workspace (else W == NULL)
+    CycleGraph graphs[kCycleGraphs];  // configurations run and their captured cycles, replaced round-robin
+    int next_graph = 0;
 };
 
 void free_solver_cache(dieop_s* op);   // the operator's context and its batch contexts
@@ -60,6 +80,7 @@ void free_red_scratch(RedScratch* rs);
 
 // Deflation handle: V (r orthonormal vectors of length n) and M = T^-1 - I (Eq. (4.12)).
 struct defl_s {
+    uint64_t id = 0;            // unique identity of this handle
     uint64_t op_id = 0;
     int r = 0;
     long n = 0;

@@ -36,7 +36,8 @@ class Desc(ct.Structure):
 
 class GmresOpts(ct.Structure):
     _fields_ = [("restart", ct.c_int), ("max_iters", ct.c_int), ("tol", ct.c_double), ("regularized", ct.c_int),
-                ("use_x0", ct.c_int), ("inner", ct.c_int), ("timing", ct.c_int), ("reorth_eta", ct.c_double)]
+                ("use_x0", ct.c_int), ("inner", ct.c_int), ("timing", ct.c_int), ("reorth_eta", ct.c_double),
+                ("graph", ct.c_int)]
 
 
 class GmresReport(ct.Structure):
@@ -44,13 +45,17 @@ class GmresReport(ct.Structure):
                 ("rel_res_solved", ct.c_double), ("rel_res_orig", ct.c_double),
                 ("t_matvec", ct.c_double), ("t_orth", ct.c_double), ("t_defl", ct.c_double),
                 ("t_total", ct.c_double), ("history", ct.POINTER(ct.c_double)), ("history_cap", ct.c_int),
-                ("history_len", ct.c_int), ("n_reorth", ct.c_int)]
+                ("history_len", ct.c_int), ("n_reorth", ct.c_int), ("graph_cycles", ct.c_int)]
 
 
 class DeflOpts(ct.Structure):
     _fields_ = [("r", ct.c_int), ("r_max", ct.c_int), ("tol", ct.c_double), ("regularized", ct.c_int),
                 ("inner", ct.c_int), ("krylov_dim", ct.c_int), ("max_restarts", ct.c_int),
                 ("seed", ct.c_ulonglong)]
+
+
+ABI_VERSION = 2
+STRUCTS = (Desc, GmresOpts, GmresReport, DeflOpts)     # the order of die_abi_sizes
 
 
 EXPORTS = {
@@ -79,6 +84,7 @@ EXPORTS = {
     "die_prof_read": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_double)]),
     "die_status_str": (ct.c_char_p, [ct.c_int]),
     "die_abi_version": (ct.c_int, []),
+    "die_abi_sizes": (ct.c_int, [ct.POINTER(ct.c_longlong), ct.c_int]),
 }
 
 _LIB = None
@@ -95,8 +101,11 @@ def _lib():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        if lib.die_abi_version() != 1:
+        if lib.die_abi_version() != ABI_VERSION:
             raise RuntimeError("libdie ABI version mismatch")
+        sizes = (ct.c_longlong * 4)()
+        if lib.die_abi_sizes(sizes, 4) != 0 or list(sizes) != [ct.sizeof(t) for t in STRUCTS]:
+            raise RuntimeError("libdie structure layouts differ from the binding's")
         _LIB = lib
     return _LIB
 
@@ -254,8 +263,9 @@ class Operator:
     def solve(self, b, x=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
               regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
               timing: bool = False, history: int = 0, stream=None, raise_on_noconv: bool = False,
-              reorth_eta: float = 0.0):
-        """Restarted GMRES; returns (x, report dict).  x (complex128) may hold an initial guess."""
+              reorth_eta: float = 0.0, graph: bool = False):
+        """Restarted GMRES; returns (x, report dict).  x (complex128) may hold an initial guess.
+        graph: run each cycle's Arnoldi steps as one CUDA graph launch (captured once)."""
         import numpy as np
         import torch
         if b.dtype != torch.complex128:
@@ -264,7 +274,7 @@ class Operator:
         if x is None:
             x = torch.empty_like(b)
         opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, int(bool(timing)),
-                         float(reorth_eta))
+                         float(reorth_eta), int(bool(graph)))
         rep = GmresReport()
         hist = None
         if history > 0:
@@ -278,14 +288,14 @@ class Operator:
         out = {"status": STATUS[code], "converged": code == 0, "cycles": rep.cycles, "iters": rep.iters,
                "n_apply": rep.n_apply, "rel_res_solved": rep.rel_res_solved, "rel_res_orig": rep.rel_res_orig,
                "t_matvec": rep.t_matvec, "t_orth": rep.t_orth, "t_defl": rep.t_defl, "t_total": rep.t_total,
-               "n_reorth": rep.n_reorth}
+               "n_reorth": rep.n_reorth, "graph_cycles": rep.graph_cycles}
         if hist is not None:
             out["history"] = hist[:rep.history_len].copy()
         return x, out
 
     def solve_batch(self, B, X=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
                     regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
-                    stream=None, reorth_eta: float = 0.0):
+                    stream=None, reorth_eta: float = 0.0, graph: bool = False):
         """Concurrent restarted GMRES on the right-hand sides B[k] (complex128, shape
         (nrhs, 2, n2, n1)); returns (X, list of report dicts)."""
         import torch
@@ -297,7 +307,8 @@ class Operator:
         use_x0 = X is not None
         if X is None:
             X = torch.empty_like(B)
-        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, 0, float(reorth_eta))
+        opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, 0, float(reorth_eta),
+                         int(bool(graph)))
         reps = (GmresReport * nrhs)()
         d = deflation.handle if deflation is not None else None
         code = _lib().gmres_solve_batch(self._h, d, ct.byref(opts), nrhs, _ptr(B), _ptr(X),
@@ -309,7 +320,7 @@ class Operator:
             ok = r.rel_res_solved <= tol
             outs.append({"converged": bool(ok), "cycles": r.cycles, "iters": r.iters, "n_apply": r.n_apply,
                          "rel_res_solved": r.rel_res_solved, "rel_res_orig": r.rel_res_orig,
-                         "t_total": r.t_total, "n_reorth": r.n_reorth})
+                         "t_total": r.t_total, "n_reorth": r.n_reorth, "graph_cycles": r.graph_cycles})
         return X, outs
 
 

@@ -47,7 +47,17 @@ def test_binding_covers_every_symbol():
 def test_status_strings(lib):
     assert lib.die_status_str(0) == b"ok"
     assert b"singular" in lib.die_status_str(4)
-    assert lib.die_abi_version() == 1
+    assert lib.die_abi_version() == 2
+
+
+def test_struct_layouts_match_the_binding(lib):
+    """The ctypes mirrors of the public structures have the library's sizes."""
+    import ctypes as ct
+    from paper_1104_4263_gb300 import die
+    sizes = (ct.c_longlong * 4)()
+    assert lib.die_abi_sizes(sizes, 4) == 0
+    assert list(sizes) == [ct.sizeof(t) for t in die.STRUCTS]
+    assert lib.die_abi_sizes(None, 4) == 1 and lib.die_abi_sizes(sizes, 5) == 1
 
 
 def test_deflation_radius_host(lib):

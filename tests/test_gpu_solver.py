@@ -222,3 +222,48 @@ def test_solve_batch_equals_single_solves(inner):
             assert reps[k]["iters"] == rk["iters"]
             assert torch.equal(X[k], xk)
             assert reps[k]["converged"]
+
+
+@pytest.mark.parametrize("inner,defl_r", [(die.DIE_FP64, 0), (die.DIE_FP64, 6), (die.DIE_FP32_INNER, 0),
+                                          (die.DIE_FP32_INNER, 6)])
+def test_graph_cycles_equal_direct_launches(inner, defl_r):
+    """Cycles whose Arnoldi steps run as one captured CUDA graph give the iterates of
+    cycles launched kernel by kernel, bit for bit: on a fresh operator the first cycle runs
+    directly and the rest as graph launches; a later solve with the same configuration
+    replays the kept graph from its first cycle (compile-time FFT path and a ragged
+    general-path grid; plain, deflated, FP64 and FP32-inner)."""
+    for n1, n2 in ((128, 128), (40, 33)):
+        p = W.core_shell(max(n1, n2), side=1.5, r_core=0.3, r_shell=0.6, eps_core=2.0 + 0.1j, eps_shell=4.0 + 0.2j)
+        eps = p.eps_r[:n2, :n1].copy()
+        kw = dict(restart=10, tol=1e-9, max_iters=600, regularized=True, inner=inner)
+        op_g = die.Operator(eps, p.h)
+        Dg = die.Deflation(op_g, defl_r, tol=1e-4, regularized=True, inner=inner) if defl_r else None
+        b = op_g.plane_wave(0.4)
+        xg1, rg1 = op_g.solve(b.clone(), deflation=Dg, graph=True, **kw)
+        # the first cycle of each configuration runs directly (a cycle rerun with the
+        # second Gram-Schmidt pass is another configuration)
+        assert rg1["cycles"] >= 3 and rg1["cycles"] - 2 <= rg1["graph_cycles"] <= rg1["cycles"] - 1
+        xd, rd = op_g.solve(b.clone(), deflation=Dg, graph=False, **kw)
+        assert rd["graph_cycles"] == 0
+        xg2, rg2 = op_g.solve(b.clone(), deflation=Dg, graph=True, **kw)
+        assert rg2["graph_cycles"] == rg2["cycles"]
+        for r in (rg1, rg2):
+            assert (r["iters"], r["cycles"], r["rel_res_solved"]) == (rd["iters"], rd["cycles"], rd["rel_res_solved"])
+        assert torch.equal(xg1, xd) and torch.equal(xg2, xd)
+        assert rd["converged"]
+
+
+def test_graph_batch_equals_direct_batch():
+    """Concurrent solves (one context and host thread per right-hand side) with graph
+    cycles: each context captures in its own thread; the iterates equal the direct ones."""
+    p = W.core_shell(128, side=1.5, r_core=0.3, r_shell=0.6, eps_core=2.0 + 0.1j, eps_shell=4.0 + 0.2j)
+    op = die.Operator(p.eps_r, p.h)
+    D = die.Deflation(op, 6, tol=1e-4, regularized=True, inner=die.DIE_FP32_INNER)
+    B = torch.stack([op.plane_wave(psi) for psi in (0.0, 0.7, 2.1, 3.3)]).contiguous()
+    kw = dict(restart=10, tol=1e-9, max_iters=600, regularized=True, inner=die.DIE_FP32_INNER, deflation=D)
+    Xd, rd = op.solve_batch(B, graph=False, **kw)
+    Xg, rg = op.solve_batch(B, graph=True, **kw)
+    assert torch.equal(Xg, Xd)
+    for a, g in zip(rd, rg):
+        assert a["iters"] == g["iters"] and a["graph_cycles"] == 0 and g["graph_cycles"] == g["cycles"]
+        assert a["converged"]
