@@ -19,10 +19,10 @@ FP64 GMRES(30) on A for the same step budget; time-to-tolerance against plain FP
 problems that converge (the paper's Section 4 test squares with the Table 2
 fair-memory settings, and the 32^2 cylinder); the bare regularised product rate, alone
 and batched over 8 right-hand sides (matvec); 4 and 8 incidence angles solved one after
-another and concurrently (batch_solve); Arnoldi steps per second with each cycle launched
-kernel by kernel and as one CUDA graph, on the batched workload's grid sizes
-(graph_cycles); the roofline of the dominant kernel; the CPU oracle on this machine's
-cores.
+another and concurrently (batch_solve); Arnoldi steps per second on the batched
+workload's grid sizes, one solve and 8 concurrent angles, each with cycles launched
+kernel by kernel and as CUDA graphs (small_grids); the roofline of the dominant kernel;
+the CPU oracle on this machine's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -394,7 +394,7 @@ def main():
 
     out["matvec"] = matvec_rates(op, p, die, torch)
     out["batch_solve"] = [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)]
-    out["graph_cycles"] = graph_rates(die, W, torch)
+    out["small_grids"] = small_grid_rates(die, W, torch)
     if not args.no_compare:
         out["plain_fp64_same_budget"] = plain_fp64(op, b, args.step_iters, dt / args.steps, last)
         out["time_to_tol"] = time_to_tol(die, W, torch)
@@ -508,11 +508,13 @@ def batch_solve_rates(op, D, die, torch, nrhs: int = 4, iters: int = 300):
             "unit": UNIT, "note": "incidence angles 2 pi k / nrhs; wall time around the host calls"}
 
 
-def graph_rates(die, W, torch, sizes=(64, 96, 128, 256, 512), iters: int = 300, reps: int = 3):
-    """Arnoldi steps per second with each cycle's steps launched kernel by kernel against
-    one CUDA graph launch per cycle (gmres_opts.graph), on the Gaussian-field scatterers of
-    the batched workload (the first of each grid size): regularised, FP32-inner, GMRES(30),
-    a fixed budget of `iters` steps per solve."""
+def small_grid_rates(die, W, torch, sizes=(64, 96, 128, 256, 512), iters: int = 300, reps: int = 3,
+                     nrhs: int = 8):
+    """Arnoldi steps per second on the Gaussian-field scatterers of the batched workload
+    (the first of each grid size), regularised, FP32-inner, GMRES(30), a fixed budget of
+    `iters` steps per solve: one solve at a time with each cycle launched kernel by kernel
+    or as one CUDA graph (gmres_opts.graph), and nrhs incidence angles solved concurrently
+    (gmres_solve_batch), again direct or as graphs."""
     probs = {}
     for q in W.config3(64):
         probs.setdefault(q.n1, q)
@@ -523,23 +525,29 @@ def graph_rates(die, W, torch, sizes=(64, 96, 128, 256, 512), iters: int = 300, 
         q = probs[n]
         op = die.Operator(q.eps_r, q.h)
         b = op.plane_wave(0.0)
+        B = torch.stack([op.plane_wave(2 * math.pi * k / nrhs) for k in range(nrhs)]).contiguous()
         kw = dict(restart=RESTART, tol=1e-14, max_iters=iters, regularized=True, inner=die.DIE_FP32_INNER)
-        op.solve(b.clone(), graph=False, **kw)           # context allocated, kernels warm
-        op.solve(b.clone(), graph=True, **kw)            # graphs captured
         res = {}
+        for graph in (False, True):
+            op.solve(b.clone(), graph=graph, **kw)       # context allocated, kernels warm, graphs captured
+            op.solve_batch(B, graph=graph, **kw)
         for graph in (False, True):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            steps = 0
-            for _ in range(reps):
-                steps += op.solve(b.clone(), graph=graph, **kw)[1]["iters"]
+            steps = sum(op.solve(b.clone(), graph=graph, **kw)[1]["iters"] for _ in range(reps))
             torch.cuda.synchronize()
-            res[graph] = steps / (time.perf_counter() - t0)
-        out.append({"n": n, "unknowns": 2 * n * n, "direct_steps_per_s": res[False], "graph_steps_per_s": res[True],
-                    "speedup": res[True] / res[False]})
+            res[("single", graph)] = steps / (time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            steps = sum(sum(r["iters"] for r in op.solve_batch(B, graph=graph, **kw)[1]) for _ in range(reps))
+            torch.cuda.synchronize()
+            res[("batch", graph)] = steps / (time.perf_counter() - t0)
+        out.append({"n": n, "unknowns": 2 * n * n,
+                    "single_direct": res[("single", False)], "single_graph": res[("single", True)],
+                    f"batch{nrhs}_direct": res[("batch", False)], f"batch{nrhs}_graph": res[("batch", True)]})
         del op
     return {"unit": "Arnoldi steps/s (regularised products in the solver)", "sizes": out,
-            "note": f"{iters} steps per solve, {reps} solves each, wall time around the host calls"}
+            "note": (f"{iters} steps per solve, {reps} repetitions; batch: {nrhs} incidence angles 2 pi k / {nrhs} "
+                     "solved concurrently; wall time around the host calls")}
 
 
 def plain_fp64(op, b, step_iters, step_s, last):
