@@ -24,7 +24,11 @@
 //
 // A solve runs in a context (SolverCache): buffers, streams, deflation scratch and,
 // for the right-hand sides of gmres_solve_batch, a product workspace of its own, so
-// that several solves can run at once on one operator.
+// that several solves can run at once on one operator.  With gmres_opts.graph a
+// cycle's Arnoldi steps (and the side-stream Givens steps) are captured once into a
+// CUDA graph per configuration and replayed with one launch per cycle; what changes
+// from cycle to cycle (the history slot of the first step, ||btilde||) is read from
+// device memory, so the replay is the same launch sequence.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
