@@ -21,8 +21,9 @@ fair-memory settings, and the 32^2 cylinder); the bare regularised product rate,
 and batched over 8 right-hand sides (matvec); 4 and 8 incidence angles solved one after
 another and concurrently (batch_solve); Arnoldi steps per second on the batched
 workload's grid sizes, one solve and 8 concurrent angles, each with cycles launched
-kernel by kernel and as CUDA graphs (small_grids); the roofline of the dominant kernel;
-the CPU oracle on this machine's cores.
+kernel by kernel and as CUDA graphs (small_grids); 64 systems of 16 mixed-size
+scatterers solved one after another and together (many_systems); the roofline of the
+dominant kernel; the CPU oracle on this machine's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -395,6 +396,7 @@ def main():
     out["matvec"] = matvec_rates(op, p, die, torch)
     out["batch_solve"] = [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)]
     out["small_grids"] = small_grid_rates(die, W, torch)
+    out["many_systems"] = many_rates(die, W, torch)
     if not args.no_compare:
         out["plain_fp64_same_budget"] = plain_fp64(op, b, args.step_iters, dt / args.steps, last)
         out["time_to_tol"] = time_to_tol(die, W, torch)
@@ -548,6 +550,40 @@ def small_grid_rates(die, W, torch, sizes=(64, 96, 128, 256, 512), iters: int = 
     return {"unit": "Arnoldi steps/s (regularised products in the solver)", "sizes": out,
             "note": (f"{iters} steps per solve, {reps} repetitions; batch: {nrhs} incidence angles 2 pi k / {nrhs} "
                      "solved concurrently; wall time around the host calls")}
+
+
+def many_rates(die, W, torch, count: int = 16, n_angles: int = 4, iters: int = 200):
+    """The batched workload's first `count` scatterers (mixed grid sizes) under n_angles
+    incidence angles each: the count x n_angles systems solved one after another
+    (gmres_solve) and all together (gmres_solve_many, cycles direct and as graphs);
+    regularised, FP32-inner, GMRES(30), a fixed budget of `iters` Arnoldi steps each."""
+    probs = W.config3(64)[:count]
+    ops, bs = [], []
+    for q in probs:
+        op = die.Operator(q.eps_r, q.h)
+        for j in range(n_angles):
+            ops.append(op)
+            bs.append(op.plane_wave(2 * math.pi * j / n_angles))
+    kw = dict(restart=RESTART, tol=1e-14, max_iters=iters, regularized=True, inner=die.DIE_FP32_INNER)
+    for k in range(0, len(ops), n_angles):          # contexts allocated, kernels warm, graphs captured
+        ops[k].solve(bs[k].clone(), **kw)
+    die.solve_many(ops, bs, **kw)
+    die.solve_many(ops, bs, graph=True, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = sum(op.solve(b.clone(), **kw)[1]["iters"] for op, b in zip(ops, bs))
+    torch.cuda.synchronize()
+    rates = {"sequential": seq / (time.perf_counter() - t0)}
+    for name, graph in (("many_direct", False), ("many_graph", True)):
+        t0 = time.perf_counter()
+        _, reps = die.solve_many(ops, bs, graph=graph, **kw)
+        torch.cuda.synchronize()
+        rates[name] = sum(r["iters"] for r in reps) / (time.perf_counter() - t0)
+    sizes = sorted({q.n1 for q in probs})
+    return {"systems": len(ops), "scatterers": count, "angles": n_angles, "grid_sizes": sizes,
+            "arnoldi_steps_each": iters, "unit": "Arnoldi steps/s (regularised products in the solver)", **rates,
+            "speedup_many_graph": rates["many_graph"] / rates["sequential"],
+            "note": "wall time around the host calls; gmres_solve_many runs up to 16 systems at once"}
 
 
 def plain_fp64(op, b, step_iters, step_s, last):

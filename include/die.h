@@ -182,6 +182,20 @@ die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* opts, const vo
 die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opts* opts, int nrhs, const void* b, void* x,
                              gmres_report* reports, void* stream);
 
+/* count independent systems whose operators may differ (different scatterers and grid
+ * sizes): system k solves with ops[k] and defls[k] (defls NULL, or an array whose
+ * entries may be NULL) from b[k] into x[k] (device complex128, 2 n1 n2 of ops[k]; x[k]
+ * holds an initial guess when opts->use_x0).  One set of options for all.  Up to 16
+ * systems run at once, one host thread each, taking the systems in order from a shared
+ * counter; a thread solves in the first batch context of the system's operator that no
+ * other thread holds at that moment (created on first use and kept by the operator, as
+ * for gmres_solve_batch), so an operator keeps as many contexts as it had systems in
+ * flight at once.  Each x[k] is bit-identical to gmres_solve on b[k].  reports: NULL or count reports.  Returns as gmres_solve_batch; DIE_EINVAL for
+ * count < 1, a NULL array or entry, or any system's options or deflation handle that
+ * gmres_solve would reject (checked before any solve starts). */
+die_status gmres_solve_many(int count, const dieop_t* ops, const defl_t* defls, const gmres_opts* opts,
+                            const void* const* b, void* const* x, gmres_report* reports, void* stream);
+
 /* ----------------------------------------------------------------------------
  * Deflation (Eqs. (4.12)-(4.13)): V = orthonormal basis of the invariant subspace
  * of the r largest-magnitude eigenvalues of Atilde (Krylov-Schur Arnoldi on the

@@ -33,7 +33,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -643,6 +645,71 @@ extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opt
         });
     }
     for (auto& t : threads) t.join();
+    die_status out = DIE_OK;
+    for (die_status s : status)
+        if (s != DIE_OK && s != DIE_ENOCONV) return s;
+        else if (s == DIE_ENOCONV) out = DIE_ENOCONV;
+    return out;
+}
+
+// Systems of different operators (grid sizes) solved concurrently: up to kMaxBatchSolve
+// host threads take the systems in order from a shared counter.  A thread solves in the
+// first batch context of the system's operator that no other thread holds at that
+// moment, so an operator keeps only as many contexts as it had systems in flight.
+extern "C" die_status gmres_solve_many(int count, const dieop_t* ops, const defl_t* defls, const gmres_opts* o,
+                                       const void* const* b, void* const* x, gmres_report* reps, void* stream) {
+    if (count < 1 || !ops || !o || !b || !x) return DIE_EINVAL;
+    for (int k = 0; k < count; k++) {
+        if (!ops[k] || !b[k] || !x[k]) return DIE_EINVAL;
+        if (!opts_valid(ops[k], defls ? defls[k] : nullptr, o)) return DIE_EINVAL;
+    }
+    int dev = 0;
+    DIE_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<dieop_s*> uniq;             // distinct operators, and the slots held in each
+    std::vector<unsigned> held;
+    std::vector<int> which(count);
+    for (int k = 0; k < count; k++) {
+        int u = 0;
+        while (u < (int)uniq.size() && uniq[u] != ops[k]) u++;
+        if (u == (int)uniq.size()) {
+            uniq.push_back(ops[k]);
+            held.push_back(0u);
+        }
+        which[k] = u;
+    }
+    const int nthreads = count < kMaxBatchSolve ? count : kMaxBatchSolve;
+    std::mutex mu;
+    std::vector<die_status> status(count, DIE_OK);
+    std::atomic<int> next{0};
+    std::atomic<bool> no_device{false};
+    std::vector<std::thread> threads;
+    threads.reserve(nthreads);
+    for (int w = 0; w < nthreads; w++) {
+        threads.emplace_back([&] {
+            if (cudaSetDevice(dev) != cudaSuccess) { no_device = true; return; }
+            for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+                dieop_s* op = ops[k];
+                const int u = which[k];
+                int slot = 0;
+                {   // at most nthreads <= kMaxBatchSolve slots are held at once: one is free
+                    std::lock_guard<std::mutex> lock(mu);
+                    while (held[u] & (1u << slot)) slot++;
+                    held[u] |= 1u << slot;
+                }
+                SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[slot]);
+                die_status s = ensure_cache(&c, op, o->restart, hist_cap_of(o), true);
+                op->batch[slot] = c;
+                if (s == DIE_OK)
+                    s = solve_ctx(op, defls ? defls[k] : nullptr, o, b[k], x[k], reps ? reps + k : nullptr,
+                                  (cudaStream_t)stream, c, false);
+                status[k] = s;
+                std::lock_guard<std::mutex> lock(mu);
+                held[u] &= ~(1u << slot);
+            }
+        });
+    }
+    for (auto& t : threads) t.join();
+    if (no_device) return DIE_ECUDA;
     die_status out = DIE_OK;
     for (die_status s : status)
         if (s != DIE_OK && s != DIE_ENOCONV) return s;

@@ -71,6 +71,8 @@ EXPORTS = {
                                ct.POINTER(GmresReport), ct.c_void_p]),
     "gmres_solve_batch": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_int, ct.c_void_p,
                                      ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "gmres_solve_many": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p,
+                                    ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "deflation_build": (ct.c_int, [ct.c_void_p, ct.POINTER(DeflOpts), ct.c_void_p, ct.POINTER(ct.c_void_p),
                                    ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
     "deflation_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -366,3 +368,38 @@ class Deflation:
             self.close()
         except Exception:
             pass
+
+
+def solve_many(ops, bs, deflations=None, xs=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
+               regularized: bool = False, inner: int = DIE_FP64, stream=None, reorth_eta: float = 0.0,
+               graph: bool = False):
+    """Concurrent restarted GMRES on systems of different operators (gmres_solve_many):
+    system k solves ops[k] with deflations[k] (or None) from bs[k] (complex128 CUDA tensor
+    of shape (2, n2, n1) of ops[k]); xs: None or initial guesses.  Returns (xs, reports)."""
+    import torch
+    count = len(ops)
+    if len(bs) != count or (deflations is not None and len(deflations) != count):
+        raise ValueError("ops, bs and deflations must have the same length")
+    for op, b in zip(ops, bs):
+        if b.dtype != torch.complex128 or not b.is_cuda or not b.is_contiguous() or b.numel() != 2 * op.N:
+            raise TypeError("solve_many takes contiguous complex128 CUDA tensors of 2 * n1 * n2 values")
+    use_x0 = xs is not None
+    xs = [torch.empty_like(b) for b in bs] if xs is None else list(xs)
+    opts = GmresOpts(restart, max_iters, tol, int(bool(regularized)), int(use_x0), inner, 0, float(reorth_eta),
+                     int(bool(graph)))
+    hops = (ct.c_void_p * count)(*[op.handle for op in ops])
+    hdef = None
+    if deflations is not None:
+        hdef = (ct.c_void_p * count)(*[d.handle if d is not None else None for d in deflations])
+    pb = (ct.c_void_p * count)(*[_ptr(b) for b in bs])
+    px = (ct.c_void_p * count)(*[_ptr(x) for x in xs])
+    reps = (GmresReport * count)()
+    code = _lib().gmres_solve_many(count, ct.cast(hops, ct.c_void_p), ct.cast(hdef, ct.c_void_p) if hdef else None,
+                                   ct.byref(opts), ct.cast(pb, ct.c_void_p), ct.cast(px, ct.c_void_p),
+                                   ct.cast(reps, ct.c_void_p), _stream(stream))
+    if code not in (0, 5):
+        raise DieError(code, "gmres_solve_many")
+    outs = [{"converged": bool(r.rel_res_solved <= tol), "cycles": r.cycles, "iters": r.iters,
+             "n_apply": r.n_apply, "rel_res_solved": r.rel_res_solved, "rel_res_orig": r.rel_res_orig,
+             "t_total": r.t_total, "n_reorth": r.n_reorth, "graph_cycles": r.graph_cycles} for r in reps]
+    return xs, outs

@@ -91,3 +91,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         assert lib.gmres_solve_batch(dummy, None, ct.byref(opts), nrhs, dummy, dummy, None, None) == 1
     for nrhs in (0, 1025):                        # outside [1, 1024]
         assert lib.dieop_apply_batch(dummy, nrhs, dummy, dummy, 1, None) == 1
+    assert lib.gmres_solve_many(0, dummy, None, ct.byref(opts), dummy, dummy, None, None) == 1
+    assert lib.gmres_solve_many(1, None, None, ct.byref(opts), dummy, dummy, None, None) == 1
+    nulls = ct.cast((ct.c_void_p * 1)(None), ct.c_void_p)     # ops[0] == NULL
+    assert lib.gmres_solve_many(1, nulls, None, ct.byref(opts), nulls, nulls, None, None) == 1

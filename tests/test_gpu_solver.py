@@ -267,3 +267,27 @@ def test_graph_batch_equals_direct_batch():
     for a, g in zip(rd, rg):
         assert a["iters"] == g["iters"] and a["graph_cycles"] == 0 and g["graph_cycles"] == g["cycles"]
         assert a["converged"]
+
+
+def test_solve_many_equals_single_solves():
+    """Systems of four operators of different grids (the compile-time FFT path, a 3 2^a
+    runtime-plan grid, a ragged grid, one without deflation), two incidence angles each,
+    solved concurrently by gmres_solve_many: every solution and step count equals a single
+    gmres_solve of that system."""
+    ops, bs, defls = [], [], []
+    for n1, n2, r in ((128, 128, 6), (96, 96, 6), (40, 33, 6), (64, 64, 0)):
+        p = W.core_shell(max(n1, n2), side=1.5, r_core=0.3, r_shell=0.6, eps_core=2.0 + 0.1j, eps_shell=4.0 + 0.2j)
+        eps = p.eps_r[:n2, :n1].copy()
+        op = die.Operator(eps, p.h)
+        D = die.Deflation(op, r, tol=1e-4, regularized=True, inner=die.DIE_FP32_INNER) if r else None
+        for psi in (0.3, 1.9):
+            ops.append(op)
+            bs.append(op.plane_wave(psi))
+            defls.append(D)
+    kw = dict(restart=20, tol=1e-7, max_iters=4000, regularized=True, inner=die.DIE_FP32_INNER)
+    xs, reps = die.solve_many(ops, bs, deflations=defls, **kw)
+    for k in range(len(ops)):
+        xk, rk = ops[k].solve(bs[k].clone(), deflation=defls[k], **kw)
+        assert reps[k]["iters"] == rk["iters"]
+        assert torch.equal(xs[k], xk)
+        assert reps[k]["converged"]
