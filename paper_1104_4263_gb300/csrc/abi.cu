@@ -211,7 +211,12 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
     if (desc->prec != DIE_FP64 && desc->prec != DIE_FP32_INNER) return DIE_EINVAL;
     dieop_s* op = new (std::nothrow) dieop_s();
     if (!op) return DIE_ENOMEM;
-    die_status s = create_impl(desc, eps_r, eps_on_device, (cudaStream_t)stream, op);
+    die_status s;
+    try {
+        s = create_impl(desc, eps_r, eps_on_device, (cudaStream_t)stream, op);
+    } catch (...) {               // host allocation failure: no exception crosses the C ABI
+        s = DIE_ENOMEM;
+    }
     if (s != DIE_OK) { free_op(op); return s; }
     *out = op;
     return DIE_OK;

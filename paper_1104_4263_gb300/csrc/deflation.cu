@@ -314,7 +314,12 @@ extern "C" die_status deflation_build(dieop_t op, const defl_opts* o, void* stre
     if (o->r > 0 && 2L * op->N <= o->r + 2) return DIE_EINVAL;
     defl_s* d = new (std::nothrow) defl_s();
     if (!d) return DIE_ENOMEM;
-    const die_status s = build_impl(op, o, (cudaStream_t)stream, d, eig_out, r_out);
+    die_status s;
+    try {
+        s = build_impl(op, o, (cudaStream_t)stream, d, eig_out, r_out);
+    } catch (...) {               // host allocation failure: no exception crosses the C ABI
+        s = DIE_ENOMEM;
+    }
     if (s != DIE_OK && s != DIE_ENOCONV) {
         free_defl(d);
         return s;

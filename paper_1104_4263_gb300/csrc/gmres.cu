@@ -613,17 +613,19 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
                                   gmres_report* rep, void* stream) {
     if (!op || !o || !b_ || !x_) return DIE_EINVAL;
     if (!opts_valid(op, defl, o)) return DIE_EINVAL;
-    DIE_TRY(ensure_solver_cache(op, o->restart, hist_cap_of(o)));
-    return solve_ctx(op, defl, o, b_, x_, rep, (cudaStream_t)stream, solver_cache(op), true);
+    try {                         // host allocation failure: no exception crosses the C ABI
+        DIE_TRY(ensure_solver_cache(op, o->restart, hist_cap_of(o)));
+        return solve_ctx(op, defl, o, b_, x_, rep, (cudaStream_t)stream, solver_cache(op), true);
+    } catch (...) {
+        return DIE_ENOMEM;
+    }
 }
 
 // Right-hand sides solved concurrently: one context (buffers, product workspace, deflation
 // scratch, streams) and one host thread per right-hand side, so that the FP64-bound
 // Gram-Schmidt passes of one system and the FFT passes of another share the GPU.
-extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opts* o, int nrhs, const void* b_,
-                                        void* x_, gmres_report* reps, void* stream) {
-    if (!op || !o || !b_ || !x_ || nrhs < 1 || nrhs > kMaxBatchSolve) return DIE_EINVAL;
-    if (!opts_valid(op, defl, o)) return DIE_EINVAL;
+static die_status solve_batch_impl(dieop_s* op, defl_s* defl, const gmres_opts* o, int nrhs, const void* b_,
+                                   void* x_, gmres_report* reps, void* stream) {
     const long n = 2L * op->N;
     for (int k = 0; k < nrhs; k++) {
         SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[k]);
@@ -637,12 +639,21 @@ extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opt
     std::vector<std::thread> threads;
     threads.reserve(nrhs);
     for (int k = 0; k < nrhs; k++) {
-        threads.emplace_back([&, k] {
-            if (cudaSetDevice(dev) != cudaSuccess) { status[k] = DIE_ECUDA; return; }
-            status[k] = solve_ctx(op, defl, o, (const double2*)b_ + k * n, (double2*)x_ + k * n,
-                                  reps ? reps + k : nullptr, (cudaStream_t)stream,
-                                  reinterpret_cast<SolverCache*>(op->batch[k]), false);
-        });
+        try {
+            threads.emplace_back([&, k] {
+                try {
+                    if (cudaSetDevice(dev) != cudaSuccess) { status[k] = DIE_ECUDA; return; }
+                    status[k] = solve_ctx(op, defl, o, (const double2*)b_ + k * n, (double2*)x_ + k * n,
+                                          reps ? reps + k : nullptr, (cudaStream_t)stream,
+                                          reinterpret_cast<SolverCache*>(op->batch[k]), false);
+                } catch (...) {
+                    status[k] = DIE_ENOMEM;
+                }
+            });
+        } catch (...) {           // no thread for systems k .. nrhs - 1
+            for (int q = k; q < nrhs; q++) status[q] = DIE_ENOMEM;
+            break;
+        }
     }
     for (auto& t : threads) t.join();
     die_status out = DIE_OK;
@@ -652,17 +663,23 @@ extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opt
     return out;
 }
 
+extern "C" die_status gmres_solve_batch(dieop_t op, defl_t defl, const gmres_opts* o, int nrhs, const void* b_,
+                                        void* x_, gmres_report* reps, void* stream) {
+    if (!op || !o || !b_ || !x_ || nrhs < 1 || nrhs > kMaxBatchSolve) return DIE_EINVAL;
+    if (!opts_valid(op, defl, o)) return DIE_EINVAL;
+    try {                         // host allocation failure before the threads start
+        return solve_batch_impl(op, defl, o, nrhs, b_, x_, reps, stream);
+    } catch (...) {
+        return DIE_ENOMEM;
+    }
+}
+
 // Systems of different operators (grid sizes) solved concurrently: up to kMaxBatchSolve
 // host threads take the systems in order from a shared counter.  A thread solves in the
 // first batch context of the system's operator that no other thread holds at that
 // moment, so an operator keeps only as many contexts as it had systems in flight.
-extern "C" die_status gmres_solve_many(int count, const dieop_t* ops, const defl_t* defls, const gmres_opts* o,
-                                       const void* const* b, void* const* x, gmres_report* reps, void* stream) {
-    if (count < 1 || !ops || !o || !b || !x) return DIE_EINVAL;
-    for (int k = 0; k < count; k++) {
-        if (!ops[k] || !b[k] || !x[k]) return DIE_EINVAL;
-        if (!opts_valid(ops[k], defls ? defls[k] : nullptr, o)) return DIE_EINVAL;
-    }
+static die_status solve_many_impl(int count, const dieop_t* ops, const defl_t* defls, const gmres_opts* o,
+                                  const void* const* b, void* const* x, gmres_report* reps, void* stream) {
     int dev = 0;
     DIE_CUDA_TRY(cudaGetDevice(&dev));
     std::vector<dieop_s*> uniq;             // distinct operators, and the slots held in each
@@ -685,29 +702,39 @@ extern "C" die_status gmres_solve_many(int count, const dieop_t* ops, const defl
     std::vector<std::thread> threads;
     threads.reserve(nthreads);
     for (int w = 0; w < nthreads; w++) {
-        threads.emplace_back([&] {
-            if (cudaSetDevice(dev) != cudaSuccess) { no_device = true; return; }
-            for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
-                dieop_s* op = ops[k];
-                const int u = which[k];
-                int slot = 0;
-                {   // at most nthreads <= kMaxBatchSolve slots are held at once: one is free
+        try {
+            threads.emplace_back([&] {
+                if (cudaSetDevice(dev) != cudaSuccess) { no_device = true; return; }
+                for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+                    dieop_s* op = ops[k];
+                    const int u = which[k];
+                    int slot = 0;
+                    {   // at most nthreads <= kMaxBatchSolve slots are held at once: one is free
+                        std::lock_guard<std::mutex> lock(mu);
+                        while (held[u] & (1u << slot)) slot++;
+                        held[u] |= 1u << slot;
+                    }
+                    die_status s;
+                    try {
+                        SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[slot]);
+                        s = ensure_cache(&c, op, o->restart, hist_cap_of(o), true);
+                        op->batch[slot] = c;
+                        if (s == DIE_OK)
+                            s = solve_ctx(op, defls ? defls[k] : nullptr, o, b[k], x[k], reps ? reps + k : nullptr,
+                                          (cudaStream_t)stream, c, false);
+                    } catch (...) {
+                        s = DIE_ENOMEM;
+                    }
+                    status[k] = s;
                     std::lock_guard<std::mutex> lock(mu);
-                    while (held[u] & (1u << slot)) slot++;
-                    held[u] |= 1u << slot;
+                    held[u] &= ~(1u << slot);
                 }
-                SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[slot]);
-                die_status s = ensure_cache(&c, op, o->restart, hist_cap_of(o), true);
-                op->batch[slot] = c;
-                if (s == DIE_OK)
-                    s = solve_ctx(op, defls ? defls[k] : nullptr, o, b[k], x[k], reps ? reps + k : nullptr,
-                                  (cudaStream_t)stream, c, false);
-                status[k] = s;
-                std::lock_guard<std::mutex> lock(mu);
-                held[u] &= ~(1u << slot);
-            }
-        });
+            });
+        } catch (...) {           // fewer threads: the ones running take every system
+            break;
+        }
     }
+    if (threads.empty()) return DIE_ENOMEM;
     for (auto& t : threads) t.join();
     if (no_device) return DIE_ECUDA;
     die_status out = DIE_OK;
@@ -715,4 +742,18 @@ extern "C" die_status gmres_solve_many(int count, const dieop_t* ops, const defl
         if (s != DIE_OK && s != DIE_ENOCONV) return s;
         else if (s == DIE_ENOCONV) out = DIE_ENOCONV;
     return out;
+}
+
+extern "C" die_status gmres_solve_many(int count, const dieop_t* ops, const defl_t* defls, const gmres_opts* o,
+                                       const void* const* b, void* const* x, gmres_report* reps, void* stream) {
+    if (count < 1 || !ops || !o || !b || !x) return DIE_EINVAL;
+    for (int k = 0; k < count; k++) {
+        if (!ops[k] || !b[k] || !x[k]) return DIE_EINVAL;
+        if (!opts_valid(ops[k], defls ? defls[k] : nullptr, o)) return DIE_EINVAL;
+    }
+    try {                         // host allocation failure before the threads start
+        return solve_many_impl(count, ops, defls, o, b, x, reps, stream);
+    } catch (...) {
+        return DIE_ENOMEM;
+    }
 }

@@ -29,7 +29,12 @@ cudaEvent_t next_event() {
         if (g_pool.size() >= kMaxEvents) return nullptr;
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
-        g_pool.push_back(e);
+        try {
+            g_pool.push_back(e);
+        } catch (...) {
+            cudaEventDestroy(e);
+            return nullptr;
+        }
     }
     return g_pool[g_used++];
 }
@@ -50,7 +55,11 @@ void prof_mark(int id, cudaStream_t st, int stop) {
     cudaEvent_t e = next_event();
     if (!e) { g_overflow = true; g_open_ev = nullptr; return; }
     cudaEventRecord(e, st);
-    g_recs.push_back(Rec{id, g_open_ev, e});
+    try {
+        g_recs.push_back(Rec{id, g_open_ev, e});
+    } catch (...) {
+        g_overflow = true;
+    }
     g_open_ev = nullptr;
 }
 
