@@ -42,7 +42,7 @@ extern "C" {
 typedef enum die_status {
     DIE_OK = 0,
     DIE_EINVAL = 1,        /* bad argument (sizes, NULL pointer, unsupported option)          */
-    DIE_ENOMEM = 2,        /* device or host allocation failed                                 */
+    DIE_ENOMEM = 2,        /* device or host allocation (or a host thread) could not be had    */
     DIE_ECUDA = 3,         /* a CUDA runtime call failed                                       */
     DIE_ESINGULAR = 4,     /* eps_r == 0 somewhere (existence condition, Eq. (3.17)), or T singular */
     DIE_ENOCONV = 5,       /* GMRES / eigensolver stopped at max_iters without reaching tol    */
@@ -164,7 +164,9 @@ typedef struct gmres_report {
 /* b, x: device complex128, 2*n1*n2.  defl may be NULL.  report may be NULL.
  * Returns DIE_OK when converged, DIE_ENOCONV at max_iters (x holds the last iterate),
  * DIE_ENAN if a norm became NaN/Inf, DIE_EBREAKDOWN on a singular Hessenberg system,
- * DIE_EINVAL on bad options (restart range, defl built for another operator). */
+ * DIE_EINVAL on bad options (restart range, defl built for another operator), DIE_ENOMEM
+ * when the solver context cannot be allocated, DIE_ECUDA on a CUDA error.  No call of
+ * this library lets a C++ exception escape. */
 die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* opts, const void* b, void* x,
                        gmres_report* report, void* stream);
 
