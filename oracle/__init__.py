@@ -18,7 +18,9 @@ preconditioning", that it follows):
   fftmv      -- the same product through a zero-padded 2-D FFT (scipy.fft); the
                 CPU throughput baseline for grids too large for the dense matrix.
   rows       -- exact O(N) sums for selected output rows on large grids.
-  gmres      -- restarted GMRES(m) with right preconditioning (Section 4/5).
+  gmres      -- restarted GMRES(m) with right preconditioning (Section 4/5), and
+                flexible GMRES (Saad 1993) for a step-dependent or nonlinear right
+                preconditioner such as a learned one.
   deflation  -- the deflating preconditioner of Eqs. (4.12)-(4.13) built from a
                 dense eigendecomposition; the deflation radius of Section 5.
   cylinder   -- closed-form series for TE scattering by a homogeneous circular

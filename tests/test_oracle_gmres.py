@@ -104,3 +104,45 @@ def test_regularised_deflated_beats_plain_under_restart():
     reg = gmres.gmres(lambda v: dense.matvec(AR @ A, v), dense.matvec(AR, b), 60, 1e-10, 1500,
                       precond=D.apply)
     assert not plain.converged and reg.converged and reg.iters < 600
+
+
+def _random_system(seed, n=48):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 2 + 0.8 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return rng, A, b
+
+
+def test_fgmres_with_fixed_preconditioner_is_right_preconditioned_gmres():
+    """Flexible GMRES with one linear preconditioner for every step takes the iterates of
+    right-preconditioned GMRES (the same Krylov space of A M, the same minimisation)."""
+    rng, A, b = _random_system(11)
+    Mx = np.eye(48) + 0.3 * rng.standard_normal((48, 48)) / math.sqrt(48)
+    kw = dict(restart=7, tol=1e-10, max_iters=400)
+    ref = gmres.gmres(lambda x: A @ x, b, precond=lambda v: Mx @ v, **kw)
+    got = gmres.fgmres(lambda x: A @ x, b, precond=lambda v, j: Mx @ v, **kw)
+    assert (got.iters, got.cycles) == (ref.iters, ref.cycles)
+    assert np.allclose(got.history, ref.history, rtol=1e-9, atol=1e-15)
+    assert np.linalg.norm(got.x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    plain = gmres.gmres(lambda x: A @ x, b, **kw)
+    ident = gmres.fgmres(lambda x: A @ x, b, **kw)
+    assert ident.iters == plain.iters and np.allclose(ident.x, plain.x, rtol=1e-10, atol=1e-14)
+
+
+def test_full_fgmres_with_a_nonlinear_preconditioner_is_exact():
+    """With a preconditioner that changes every step (here a nonlinear map of v and j) the
+    full flexible method still minimises the residual over the span of its z_j: with as
+    many steps as unknowns it returns the solution of A x = b."""
+    rng, A, b = _random_system(12, n=30)
+    B = rng.standard_normal((30, 30)) / math.sqrt(30)
+
+    def nonlinear(v, j):
+        return v + 0.2 * np.tanh(np.abs(B @ v)) * v * (1 + 0.1 * j)
+
+    res = gmres.fgmres(lambda x: A @ x, b, restart=30, tol=1e-13, max_iters=30, precond=nonlinear)
+    assert res.converged
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) <= 1e-11 * np.linalg.norm(res.x)
+    # the residual estimates are those of the minimisation: non-increasing within the cycle
+    assert np.all(np.diff(res.history) <= 1e-14)
+    # and the last estimate is the true residual
+    assert abs(res.history[-1] - res.rel_res) <= 1e-10
