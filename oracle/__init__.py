@@ -23,6 +23,9 @@ preconditioning", that it follows):
                 preconditioner such as a learned one.
   deflation  -- the deflating preconditioner of Eqs. (4.12)-(4.13) built from a
                 dense eigendecomposition; the deflation radius of Section 5.
+  fno        -- Fourier neural operator (Li et al., ICLR 2021), forward and a
+                hand-derived backward pass: the reference for the learned
+                preconditioner of flexible GMRES.
   cylinder   -- closed-form series for TE scattering by a homogeneous circular
                 cylinder (textbook separation of variables in the Maxwell system
                 of Eq. (2.1)); a pin for the discretisation.
