@@ -34,6 +34,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <new>
 #include <chrono>
 #include <mutex>
 #include <thread>
@@ -78,7 +79,8 @@ static void free_cache(SolverCache* c) {
     free_red_scratch(&c->rs);
     free_red_scratch(&c->ds.rs);
     if (c->host) cudaFreeHost(c->host);
-    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {c->join[0], c->join[1], c->fork, c->back})
         if (e) cudaEventDestroy(e);
     for (CycleGraph& g : c->graphs)
@@ -101,18 +103,10 @@ void free_solver_cache(dieop_s* op) {
 static size_t small_count(int m) { return (size_t)(m + 1) * m + 2 * m + 2 * (m + 3) + 2 * (size_t)m * (m + 3) + 3 * m + 16; }
 static int ints_count(int m) { return 8 + m; }
 
-die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bool own_ws) {
-    SolverCache* c = *slot;
+// Buffers, streams and events of a new context for GMRES(m) with hist_cap history
+// entries; on failure the caller frees what was made (free_cache handles any subset).
+static die_status init_cache(SolverCache* c, dieop_s* op, int m, int hist_cap, bool own_ws) {
     const long n = 2L * op->N;
-    if (c && c->m_cap >= m && c->hist_cap >= hist_cap) return DIE_OK;
-    if (c) {
-        m = m > c->m_cap ? m : c->m_cap;
-        hist_cap = hist_cap > c->hist_cap ? hist_cap : c->hist_cap;
-        free_cache(c);
-        *slot = nullptr;
-    }
-    c = new SolverCache();
-    *slot = c;
     c->m_cap = m;
     c->n = n;
     c->hist_cap = hist_cap;
@@ -131,20 +125,12 @@ die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bo
         c->ws.v_bytes = op->ws.v_bytes;
         ok = al(&c->ws.W, c->ws.W_bytes) && al(&c->ws.v, c->ws.v_bytes);
     }
-    if (!ok) {
+    if (!ok || cudaHostAlloc((void**)&c->host, 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
-        free_cache(c);
-        *slot = nullptr;
         return DIE_ENOMEM;
     }
     DIE_TRY(alloc_red_scratch(&c->rs));
     DIE_TRY(alloc_red_scratch(&c->ds.rs));
-    if (cudaHostAlloc((void**)&c->host, 64 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
-        cudaGetLastError();
-        free_cache(c);
-        *slot = nullptr;
-        return DIE_ENOMEM;
-    }
     const double2 one = make_double2(1.0, 0.0);
     DIE_CUDA_TRY(cudaMemcpy(c->one, &one, sizeof one, cudaMemcpyHostToDevice));
     DIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -152,8 +138,32 @@ die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bo
     for (auto& e : c->join) DIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->back, cudaEventDisableTiming));
-    c->ev.resize(4 * (size_t)(m + 1));
+    try {
+        c->ev.resize(4 * (size_t)(m + 1));       // null handles until created
+    } catch (...) {
+        return DIE_ENOMEM;
+    }
     for (auto& e : c->ev) DIE_CUDA_TRY(cudaEventCreate(&e));
+    return DIE_OK;
+}
+
+die_status ensure_cache(SolverCache** slot, dieop_s* op, int m, int hist_cap, bool own_ws) {
+    SolverCache* c = *slot;
+    if (c && c->m_cap >= m && c->hist_cap >= hist_cap) return DIE_OK;
+    if (c) {
+        m = m > c->m_cap ? m : c->m_cap;
+        hist_cap = hist_cap > c->hist_cap ? hist_cap : c->hist_cap;
+        free_cache(c);
+        *slot = nullptr;
+    }
+    c = new (std::nothrow) SolverCache();
+    if (!c) return DIE_ENOMEM;
+    const die_status s = init_cache(c, op, m, hist_cap, own_ws);
+    if (s != DIE_OK) {            // a context is published only once complete
+        free_cache(c);
+        return s;
+    }
+    *slot = c;
     return DIE_OK;
 }
 
