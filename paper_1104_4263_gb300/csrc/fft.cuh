@@ -119,13 +119,32 @@ __host__ __device__ __forceinline__ void dft(V* x) {
 __host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 4); }
 
+// Twiddle load: read-only cache path on the device, plain load on the host (the stage
+// code also runs on the host, where a CPU test checks it against a plain DFT).
+template <typename V> __host__ __device__ __forceinline__ V ld_tw(const V* p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// 1 + index of the lowest set bit (0 for x == 0)
+__host__ __device__ __forceinline__ int ffs_int(int x) {
+#ifdef __CUDA_ARCH__
+    return __ffs(x);
+#else
+    return __builtin_ffs(x);
+#endif
+}
+
 // j mod Ns (Ns is a power of two for 2^a transforms, possibly 3 * 2^b otherwise)
-__device__ __forceinline__ int mod_ns(int j, int Ns) { return (Ns & (Ns - 1)) == 0 ? (j & (Ns - 1)) : j % Ns; }
+__host__ __device__ __forceinline__ int mod_ns(int j, int Ns) { return (Ns & (Ns - 1)) == 0 ? (j & (Ns - 1)) : j % Ns; }
 // Thread t of a group of G threads handles butterflies j = t + b G, b < EPT/R.
 // Register x[b * R + r] holds input r of butterfly b.
 
 template <typename V, int EPT, int R>
-__device__ __forceinline__ void stage_load(const V* __restrict__ buf, V (&x)[EPT], int L, int t, int G) {
+__host__ __device__ __forceinline__ void stage_load(const V* __restrict__ buf, V (&x)[EPT], int L, int t, int G) {
     constexpr int B = EPT / R;
     const int LR = L / R;
 #pragma unroll
@@ -137,7 +156,7 @@ __device__ __forceinline__ void stage_load(const V* __restrict__ buf, V (&x)[EPT
 }
 
 template <typename V, int EPT, int R, bool INV>
-__device__ __forceinline__ void stage_compute(V (&x)[EPT], int L, int Ns, int t, int G, const V* __restrict__ tw) {
+__host__ __device__ __forceinline__ void stage_compute(V (&x)[EPT], int L, int Ns, int t, int G, const V* __restrict__ tw) {
     constexpr int B = EPT / R;
 #pragma unroll
     for (int b = 0; b < B; b++) {
@@ -145,10 +164,10 @@ __device__ __forceinline__ void stage_compute(V (&x)[EPT], int L, int Ns, int t,
         if (Ns > 1) {
             const int k = mod_ns(j, Ns);
             const int LR = L / R;
-            const int step = ((Ns & (Ns - 1)) == 0 ? (LR >> (__ffs(Ns) - 1)) : LR / Ns) * k;
+            const int step = ((Ns & (Ns - 1)) == 0 ? (LR >> (ffs_int(Ns) - 1)) : LR / Ns) * k;
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                V w = __ldg(&tw[r * step]);
+                V w = ld_tw(&tw[r * step]);
                 if (INV) w.y = -w.y;
                 x[b * R + r] = cmul(x[b * R + r], w);
             }
@@ -158,7 +177,7 @@ __device__ __forceinline__ void stage_compute(V (&x)[EPT], int L, int Ns, int t,
 }
 
 template <typename V, int EPT, int R>
-__device__ __forceinline__ void stage_store(V* __restrict__ buf, const V (&x)[EPT], int L, int Ns, int t, int G) {
+__host__ __device__ __forceinline__ void stage_store(V* __restrict__ buf, const V (&x)[EPT], int L, int Ns, int t, int G) {
     constexpr int B = EPT / R;
 #pragma unroll
     for (int b = 0; b < B; b++) {
@@ -172,7 +191,7 @@ __device__ __forceinline__ void stage_store(V* __restrict__ buf, const V (&x)[EP
 
 // Dispatch helpers over the runtime radix (EPT = 16: R in {2,4,8,16}; EPT = 12: R in {2,3,4}).
 template <typename V, int EPT, bool INV>
-__device__ __forceinline__ void compute_any(int R, V (&x)[EPT], int L, int Ns, int t, int G, const V* tw) {
+__host__ __device__ __forceinline__ void compute_any(int R, V (&x)[EPT], int L, int Ns, int t, int G, const V* tw) {
     if constexpr (EPT % 16 == 0) { if (R == 16) { stage_compute<V, EPT, 16, INV>(x, L, Ns, t, G, tw); return; } }
     if constexpr (EPT % 8 == 0) { if (R == 8) { stage_compute<V, EPT, 8, INV>(x, L, Ns, t, G, tw); return; } }
     if constexpr (EPT % 4 == 0) { if (R == 4) { stage_compute<V, EPT, 4, INV>(x, L, Ns, t, G, tw); return; } }
@@ -181,7 +200,7 @@ __device__ __forceinline__ void compute_any(int R, V (&x)[EPT], int L, int Ns, i
 }
 
 template <typename V, int EPT>
-__device__ __forceinline__ void load_any(int R, const V* buf, V (&x)[EPT], int L, int t, int G) {
+__host__ __device__ __forceinline__ void load_any(int R, const V* buf, V (&x)[EPT], int L, int t, int G) {
     if constexpr (EPT % 16 == 0) { if (R == 16) { stage_load<V, EPT, 16>(buf, x, L, t, G); return; } }
     if constexpr (EPT % 8 == 0) { if (R == 8) { stage_load<V, EPT, 8>(buf, x, L, t, G); return; } }
     if constexpr (EPT % 4 == 0) { if (R == 4) { stage_load<V, EPT, 4>(buf, x, L, t, G); return; } }
@@ -190,7 +209,7 @@ __device__ __forceinline__ void load_any(int R, const V* buf, V (&x)[EPT], int L
 }
 
 template <typename V, int EPT>
-__device__ __forceinline__ void store_any(int R, V* buf, const V (&x)[EPT], int L, int Ns, int t, int G) {
+__host__ __device__ __forceinline__ void store_any(int R, V* buf, const V (&x)[EPT], int L, int Ns, int t, int G) {
     if constexpr (EPT % 16 == 0) { if (R == 16) { stage_store<V, EPT, 16>(buf, x, L, Ns, t, G); return; } }
     if constexpr (EPT % 8 == 0) { if (R == 8) { stage_store<V, EPT, 8>(buf, x, L, Ns, t, G); return; } }
     if constexpr (EPT % 4 == 0) { if (R == 4) { stage_store<V, EPT, 4>(buf, x, L, Ns, t, G); return; } }
@@ -201,9 +220,9 @@ __device__ __forceinline__ void store_any(int R, V* buf, const V (&x)[EPT], int 
 // Element e = b*R + r of the register array sits at natural index j + r L/R of the
 // stage's input (first stage) or output (last stage, Ns = L/R), j = t + b G.
 template <int EPT>
-__device__ __forceinline__ int reg_index(int e, int R, int L, int t, int G) {
+__host__ __device__ __forceinline__ int reg_index(int e, int R, int L, int t, int G) {
     if ((R & (R - 1)) == 0) {
-        const int lg = __ffs(R) - 1;
+        const int lg = ffs_int(R) - 1;
         return t + (e >> lg) * G + (e & (R - 1)) * (L >> lg);
     }
     const int b = e / R, r = e - b * R;

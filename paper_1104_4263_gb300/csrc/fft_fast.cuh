@@ -28,16 +28,6 @@ template <int L> struct P2 {
 };
 
 
-// Twiddle load: read-only cache path on the device, plain load on the host (the stage
-// code also runs on the host, where a CPU test checks it against a plain DFT).
-template <typename V> __host__ __device__ __forceinline__ V ld_tw(const V* p) {
-#ifdef __CUDA_ARCH__
-    return __ldg(p);
-#else
-    return *p;
-#endif
-}
-
 // (base mod 16) + (c mod 16) < 16 for every load and store of a stage (see the top of
 // the file).
 template <int L, int R, int NS>

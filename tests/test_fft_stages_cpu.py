@@ -1,11 +1,14 @@
-"""The compile-time Stockham stages of the product kernels, run on the host.
+"""The Stockham stages of the product kernels, run on the host.
 
-The stage code of `csrc/fft_fast.cuh` (stage loads, twiddles, radix-R DFTs and stores
-through the padded shared-memory layout) is host-callable.  `fft_stages_host.cu` runs every
-thread of a transform group through each plan of the fast path (L = 256 ... 4096, forward
-and inverse, FP64 and FP32) and compares the result with the plain DFT sum evaluated in
-long double.  This pins the FFT building blocks of the GPU path on a machine without a GPU;
-the GPU parity tests check the complete products against the oracle.
+The stage code of `csrc/fft_fast.cuh` and `csrc/fft.cuh` (stage loads, twiddles, radix-R
+DFTs and stores through the padded shared-memory layout) is host-callable.
+`fft_stages_host.cu` runs every thread of a transform group through
+* each compile-time plan of the fast kernels (L = 256 ... 4096), and
+* the runtime-plan stages of the general kernels through the planner's plans for 2^a and
+  3 * 2^a lengths (16 or 12 values per thread),
+forward and inverse, FP64 and FP32, and compares the result with the plain DFT sum
+evaluated in long double.  This pins the FFT building blocks of the GPU path on a machine
+without a GPU; the GPU parity tests check the complete products against the oracle.
 """
 import os
 import shutil
@@ -14,7 +17,8 @@ import subprocess
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LENGTHS = (256, 512, 1024, 2048, 4096)
+LENGTHS = (256, 512, 1024, 2048, 4096)               # compile-time plans (fast kernels)
+GENERAL_LENGTHS = (16, 32, 64, 128, 512, 1024, 24, 48, 96, 192, 384, 768, 1536)   # runtime plans
 
 
 def _nvcc():
@@ -38,12 +42,13 @@ def stage_errors(tmp_path_factory):
     errs = {}
     for line in out.splitlines():
         L, direction, prec, err = line.split()
-        errs[(int(L), direction, prec)] = float(err)
+        errs[(L, direction, prec)] = float(err)
     return errs
 
 
-def test_every_fast_plan_is_run(stage_errors):
-    want = {(L, d, p) for L in LENGTHS for d in ("fwd", "inv") for p in ("f64", "f32")}
+def test_every_plan_is_run(stage_errors):
+    lengths = [str(L) for L in LENGTHS] + ["gen%d" % L for L in GENERAL_LENGTHS]
+    want = {(L, d, p) for L in lengths for d in ("fwd", "inv") for p in ("f64", "f32")}
     assert set(stage_errors) == want
 
 
