@@ -629,33 +629,7 @@ __global__ void arnoldi_finish_kernel(GmresDev S, int j) {
     const double wnorm2 = re ? S.nrm[2 * j + 1].x : S.nrm[2 * j].x;
     const double before2 = h1[j + 1].x;
     const double hn = sqrt(fmax(wnorm2, 0.0));
-    Hc[j + 1] = make_double2(hn, 0.0);
-    for (int i = 0; i < j; i++) {
-        const double c = csv[i].x;
-        const double2 s = snv[i];
-        const double2 a = Hc[i], b = Hc[i + 1];
-        Hc[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-        // -conj(s) a + c b
-        Hc[i + 1] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
-    }
-    const double2 a = Hc[j];
-    const double b = Hc[j + 1].x;
-    const double an = hypot(a.x, a.y);
-    double c;
-    double2 s;
-    if (an == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); Hc[j] = make_double2(b, 0.0); }
-    else {
-        const double rho = hypot(an, b);
-        c = an / rho;
-        s = make_double2(a.x / an * b / rho, a.y / an * b / rho);
-        Hc[j] = make_double2(a.x / an * rho, a.y / an * rho);
-    }
-    Hc[j + 1] = make_double2(0.0, 0.0);
-    S.cs[j] = make_double2(c, 0.0);
-    S.sn[j] = s;
-    const double2 gj = S.g[j];
-    S.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-    S.g[j] = make_double2(c * gj.x, c * gj.y);
+    givens_column(Hc, csv, snv, j, hn, S.cs + j, S.sn + j, S.g);
     const double est = hypot(S.g[j + 1].x, S.g[j + 1].y) / *S.bnorm;
     const int step = *S.step0 + j;
     if (step < S.hist_cap) S.hist[step] = est;

@@ -90,6 +90,43 @@ struct GmresDev {
     int m, jmax, hist_cap;
 };
 
+// One Givens step of the GMRES least-squares problem min || beta e1 - H y || (Saad &
+// Schultz): Hc[0..j] holds column j of H (the projections of step j) and hn = ||w|| its
+// subdiagonal entry.  The j earlier rotations (cosine csv[i].x, complex sine snv[i]) are
+// applied to the column; the rotation that zeroes the subdiagonal is formed, stored in
+// *cs_j, *sn_j, and applied to g[j], g[j + 1].  Hc then holds column j of R (Hc[j + 1] =
+// 0) and |g[j + 1]| is the least-squares residual after j + 1 steps.  Host and device.
+__host__ __device__ inline void givens_column(double2* Hc, const double2* csv, const double2* snv, int j, double hn,
+                                              double2* cs_j, double2* sn_j, double2* g) {
+    Hc[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; i++) {
+        const double c = csv[i].x;
+        const double2 s = snv[i];
+        const double2 a = Hc[i], b = Hc[i + 1];
+        Hc[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+        // -conj(s) a + c b
+        Hc[i + 1] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    }
+    const double2 a = Hc[j];
+    const double b = Hc[j + 1].x;
+    const double an = hypot(a.x, a.y);
+    double c;
+    double2 s;
+    if (an == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); Hc[j] = make_double2(b, 0.0); }
+    else {
+        const double rho = hypot(an, b);
+        c = an / rho;
+        s = make_double2(a.x / an * b / rho, a.y / an * b / rho);
+        Hc[j] = make_double2(a.x / an * rho, a.y / an * rho);
+    }
+    Hc[j + 1] = make_double2(0.0, 0.0);
+    *cs_j = make_double2(c, 0.0);
+    *sn_j = s;
+    const double2 gj = g[j];
+    g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    g[j] = make_double2(c * gj.x, c * gj.y);
+}
+
 // Skip flags: the kernels return at once when *skip != 0.  A "live" flag is one that
 // another stream may set while the kernel runs (the GMRES done flag, set by the Givens
 // step on its side stream): the reduction kernels then skip only their own work and
