@@ -397,13 +397,13 @@ def main():
                 out["roofline"]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16-vector "
                                                      "launch, scaled to the average launch by the algorithmic bytes")
 
-    out["matvec"] = matvec_rates(op, p, die, torch)
-    out["batch_solve"] = [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)]
-    out["small_grids"] = small_grid_rates(die, W, torch)
-    out["many_systems"] = many_rates(die, W, torch)
+    _extra(out, "matvec", lambda: matvec_rates(op, p, die, torch))
+    _extra(out, "batch_solve", lambda: [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)])
+    _extra(out, "small_grids", lambda: small_grid_rates(die, W, torch))
+    _extra(out, "many_systems", lambda: many_rates(die, W, torch))
     if not args.no_compare:
-        out["plain_fp64_same_budget"] = plain_fp64(op, b, args.step_iters, dt / args.steps, last)
-        out["time_to_tol"] = time_to_tol(die, W, torch)
+        _extra(out, "plain_fp64_same_budget", lambda: plain_fp64(op, b, args.step_iters, dt / args.steps, last))
+        _extra(out, "time_to_tol", lambda: time_to_tol(die, W, torch))
     if not args.no_cpu:
         try:
             out["cpu_baseline"] = cpu_oracle_rate(p)
@@ -414,6 +414,15 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _extra(out: dict, key: str, fn):
+    """An informational section of the JSON line, measured after the timed region: a
+    failure in it is recorded under its key instead of losing the line."""
+    try:
+        out[key] = fn()
+    except Exception as e:  # noqa: BLE001
+        out[key] = {"error": f"{type(e).__name__}: {e}"}
 
 
 def profile_driver(args):
