@@ -95,3 +95,20 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.gmres_solve_many(1, None, None, ct.byref(opts), dummy, dummy, None, None) == 1
     nulls = ct.cast((ct.c_void_p * 1)(None), ct.c_void_p)     # ops[0] == NULL
     assert lib.gmres_solve_many(1, nulls, None, ct.byref(opts), nulls, nulls, None, None) == 1
+
+
+def test_solve_many_argument_checks_without_gpu():
+    """The binding rejects mismatched lists and tensors that are not contiguous complex128
+    CUDA vectors of the operator's size before calling the library."""
+    import types
+
+    import torch
+
+    from paper_1104_4263_gb300 import die
+    op = types.SimpleNamespace(N=16, handle=None)
+    with pytest.raises(ValueError):
+        die.solve_many([op, op], [torch.zeros(2, 4, 4, dtype=torch.complex128)])
+    with pytest.raises(TypeError):            # a CPU tensor
+        die.solve_many([op], [torch.zeros(2, 4, 4, dtype=torch.complex128)])
+    with pytest.raises(TypeError):            # wrong dtype
+        die.solve_many([op], [torch.zeros(2, 4, 4, dtype=torch.complex64)])
