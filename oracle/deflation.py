@@ -32,6 +32,20 @@ def mgs(X: np.ndarray) -> np.ndarray:
     return Q
 
 
+def largest_eigs_op(apply, n: int, r: int, tol: float = 1e-10, seed: int = 0):
+    """The r eigenpairs of largest |lambda| of the linear map `apply` on C^n, by the
+    implicitly restarted Arnoldi method of ARPACK (scipy.sparse.linalg.eigs), which is
+    what the Matlab eigs of Section 5 runs; for grids whose dense matrix is too large.
+    Ordered as largest_eigs."""
+    from scipy.sparse.linalg import LinearOperator, eigs
+    rng = np.random.default_rng(seed)
+    v0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    op = LinearOperator((n, n), matvec=lambda v: np.asarray(apply(v)).reshape(-1), dtype=np.complex128)
+    w, X = eigs(op, k=r, which="LM", tol=tol, v0=v0)
+    order = sorted(range(len(w)), key=lambda i: (-abs(w[i]), i))[:r]
+    return w[order], X[:, order]
+
+
 class Deflation:
     """P^-1 = I + V (T^-1 - I) V^* for the r largest-magnitude eigenvalues of Atilde."""
 
@@ -40,6 +54,21 @@ class Deflation:
         self.V = mgs(X)
         self.T = self.V.conj().T @ Atilde @ self.V
         self.M = np.linalg.inv(self.T) - np.eye(r)
+
+    @classmethod
+    def from_operator(cls, apply, shape, r: int, tol: float = 1e-10, seed: int = 0) -> "Deflation":
+        """The same preconditioner from products only (Section 5: eigs, then the eigenvectors
+        orthonormalised by modified Gram-Schmidt, then T = V^* Atilde V from r products).
+        apply maps an array of `shape` to one of `shape`."""
+        n = int(np.prod(shape))
+        flat = lambda v: np.asarray(apply(np.asarray(v).reshape(shape))).reshape(-1)
+        self = cls.__new__(cls)
+        self.eigs, X = largest_eigs_op(flat, n, r, tol, seed)
+        self.V = mgs(X)
+        AV = np.stack([flat(self.V[:, i]) for i in range(r)], axis=1)
+        self.T = self.V.conj().T @ AV
+        self.M = np.linalg.inv(self.T) - np.eye(r)
+        return self
 
     def apply(self, x: np.ndarray) -> np.ndarray:
         shape = x.shape

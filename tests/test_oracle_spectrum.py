@@ -86,3 +86,41 @@ def test_deflation_moves_eigenvalues_to_one(regularized):
     for z in rest:
         assert np.min(np.abs(lam - z)) < 1e-8 * max(1.0, abs(z))
     assert np.min(np.abs(D.eigs)) >= np.max(np.abs(rest)) - 1e-9
+
+
+def test_deflation_from_products_equals_dense():
+    """The product-only deflation (ARPACK eigs + modified Gram-Schmidt, Section 5) gives the
+    same preconditioner as the dense eigendecomposition: P^-1 depends only on the span of
+    the r eigenvectors, and the eigenvalues agree."""
+    n, h = 10, 0.1
+    eps = W.core_shell(n, side=1.0, r_core=0.2, r_shell=0.45, eps_core=-16 + 1.5j, eps_shell=16).eps_r
+    At = dense.dense_AR(eps, h) @ dense.dense_A(eps, h)
+    r = 8
+    D = deflation.Deflation(At, r)
+    Dp = deflation.Deflation.from_operator(lambda v: dense.matvec(At, v), (2, n, n), r, tol=1e-13)
+    assert np.allclose(Dp.V.conj().T @ Dp.V, np.eye(r), atol=1e-12)
+    assert np.max(np.abs(Dp.eigs - D.eigs)) < 1e-9 * abs(D.eigs[0])
+    assert np.max(np.abs(Dp.matrix() - D.matrix())) < 1e-8
+
+
+def test_negative_core_segment_image_reaches_the_origin():
+    """Why restarted GMRES stalls on the core-shell object: the essential spectrum of A
+    contains the segment [1, eps] of every permittivity value (Eq. (3.20)); for the
+    plasma-like core eps = -2 + 0.1i that segment passes within |Im eps| / 3 = 0.0333 of
+    the origin, and its image under the regularised map of Eq. (5.3) passes closer still
+    (0.0167), because the map fixes 0.  The shell eps = 20 + 0.5i maps into the disc of
+    the deflation radius 5.514, so only eigenvalues beyond it are discrete outliers.
+    The discrete spectrum of a small grid already shows the small eigenvalues."""
+    e = -2 + 0.1j
+    t = np.linspace(0.0, 1.0, 200001)
+    seg = 1.0 + t * (e - 1.0)
+    assert np.min(np.abs(seg)) == pytest.approx(0.1 / abs(e - 1.0) * 1.0, rel=1e-3)
+    img = deflation.regularized_eig_map(seg, e)
+    assert np.min(np.abs(img)) < 0.0168 and np.min(np.abs(img)) > 0.0166
+    p = W.config2(512)
+    R = deflation.deflation_radius(np.unique(p.eps_r))
+    # close to the lossless closed form 1 + (eps - 1)^2 / (4 eps) at eps = 20 (Section 5)
+    assert R == pytest.approx(1.0 + 19.0 ** 2 / 80.0, abs=2e-3)
+    q = W.config2(24)
+    lam = np.linalg.eigvals(dense.dense_AR(q.eps_r, q.h) @ dense.dense_A(q.eps_r, q.h))
+    assert np.min(np.abs(lam)) < 0.05
