@@ -120,14 +120,16 @@ void dieop_destroy(dieop_t op);
  * Solves Atilde x = btilde with Atilde = A (regularized = 0) or A_R A and
  * btilde = A_R b (regularized = 1), right-preconditioned by the deflation
  * P^-1 of Eq. (4.12) when a defl_t is given: Atilde P^-1 v = btilde, x = P^-1 v.
- * Arnoldi by classical Gram-Schmidt with the DGKS criterion (a second pass when
- * the first removed more than half of ||w||^2), FP64; Hessenberg least squares by
+ * Arnoldi by classical Gram-Schmidt with the DGKS criterion (by default a second pass
+ * when the first removed more than half of ||w||^2), FP64; Hessenberg least squares by
  * Givens rotations, FP64, on the device.  With inner = DIE_FP32_INNER the products
  * with Atilde inside a cycle and the deflation P^-1 run in complex64 (a fixed
  * preconditioner for the whole solve); the restart residual stays FP64.
  * ------------------------------------------------------------------------- */
 typedef struct gmres_opts {
-    int restart;           /* Krylov dimension per cycle, 1..256                               */
+    int restart;           /* Krylov dimension per cycle, 1..2048 (the basis holds restart + 1
+                              FP64 vectors and their Re - Im planes: 24 (restart + 1) 2 n1 n2
+                              bytes; bases longer than 256 vectors are swept in chunks)        */
     int max_iters;         /* cap on Arnoldi steps (applications of Atilde)                    */
     double tol;            /* stop when ||btilde - Atilde x|| / ||btilde|| <= tol              */
     int regularized;       /* 0: Atilde = A; 1: Atilde = A_R A                                 */
@@ -136,9 +138,10 @@ typedef struct gmres_opts {
                               FP64 restart residual (iterative refinement)                      */
     int timing;            /* 1: fill t_matvec/t_orth/t_defl (adds stream syncs)               */
     double reorth_eta;     /* DGKS threshold: second Gram-Schmidt pass when ||w'|| < eta ||w||;
-                              <= 0 selects 0.01 (one CGS pass loses about eps ||w||/||w'|| of
-                              orthogonality: <= 2.3e-14 at 0.01); 1/sqrt(2) is the classical
-                              choice; >= 1 always re-orthogonalises                             */
+                              <= 0 selects 1/sqrt(2), the classical choice (the basis stays
+                              orthonormal to working precision at any restart); a smaller eta
+                              saves second passes but loses orthogonality as cycles grow;
+                              >= 1 always re-orthogonalises                                    */
     int graph;             /* 1: the Arnoldi steps of a cycle run as one CUDA graph launch.  A
                               configuration (operator context, deflation handle, options, cycle
                               length) is captured the first time it recurs after one direct run
@@ -169,6 +172,17 @@ typedef struct gmres_report {
  * this library lets a C++ exception escape. */
 die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* opts, const void* b, void* x,
                        gmres_report* report, void* stream);
+
+/* Copies `count` vectors of the Krylov basis held by the operator's solver context (the
+ * one gmres_solve uses), starting at basis vector `first`, to out (device, count * 2 n1 n2
+ * complex128, one vector after another); stream-ordered.  After gmres_solve returns,
+ * vectors 1 .. k-1 of the context are the orthonormal Arnoldi vectors v_1 .. v_{k-1} of
+ * the solve's last cycle (k = that cycle's Arnoldi steps; Section 4's restarted GMRES),
+ * vector 0 holds the restart residual b~ - A~x computed after that cycle and vector k
+ * the last, unnormalised, direction.  A diagnostic of the Gram-Schmidt orthogonality
+ * (||V* V - I||); the paper has no counterpart.  DIE_EINVAL: NULL pointer, no solve run
+ * on this operator yet, or [first, first + count) outside the basis (restart + 1). */
+die_status gmres_basis(dieop_t op, int first, int count, void* out, void* stream);
 
 /* nrhs independent solves with one operator and deflation handle (for example one
  * scatterer under several incidence angles), run concurrently: b, x hold nrhs complex128
@@ -235,7 +249,10 @@ die_status deflation_apply(defl_t defl, const void* x, void* z, void* stream);
  * acceptable.  Its scratch (projections, per-block and per-group partial sums and the
  * reduction's arrival counters, about 650 KB) is a static device array inside the
  * library that every GPU loading the library keeps until the process exits.
- *   - defl must have r <= 128, else DIE_EINVAL; x, z as for deflation_apply.
+ *   - defl must have r <= 128, else DIE_EINVAL; x, z as for deflation_apply; the
+ *     device current at the call must be the one defl was built on, else DIE_EINVAL.
+ *   - The array's address is looked up once per device and kept: after a
+ *     cudaDeviceReset of that device in this process the entry point must not be used.
  *   - The first call on a device looks up the array's address on that device (call
  *     it with that device current); make this first call before any stream capture.
  *   - All calls share the one array (it keeps the last call's contents; the counter

@@ -610,8 +610,12 @@ __global__ void __launch_bounds__(kRedThreads) cgs_update_defl_kernel(const doub
 // The column, the stored rotations and g_j are staged in shared memory by the whole
 // block (one global round trip instead of one per rotation), then thread 0 computes.
 // Everything it reads belongs to step j (its own slots of h1, h2, nrm and reorth).
+// Shared memory (dynamic): the column (j + 2 slots), then the j cosines and j sines.
 __global__ void arnoldi_finish_kernel(GmresDev S, int j) {
-    __shared__ double2 col[kMaxBasis + 2], csv[kMaxBasis], snv[kMaxBasis];
+    extern __shared__ double2 fin_smem[];
+    double2* col = fin_smem;
+    double2* csv = col + (j + 2);
+    double2* snv = csv + j;
     if (*S.done) return;
     const int ld = S.m + 1;
     double2* Hgl = S.H + (long)j * ld;
@@ -685,8 +689,11 @@ __global__ void to_c64_kernel(const double2* x, float2* y, long n) {
 // reciprocals of the diagonal are formed in parallel first, then y_i = g_i / R_ii and
 // the rest of g is updated by all threads at once, so the serial chain is one complex
 // multiply per column instead of a row of them.
+// Shared memory (dynamic): rhs and rd, m slots each.
 __global__ void gmres_lsq_kernel(GmresDev S) {
-    __shared__ double2 rhs[kMaxBasis], rd[kMaxBasis];
+    extern __shared__ double2 lsq_smem[];
+    double2* rhs = lsq_smem;
+    double2* rd = lsq_smem + S.m;
     const int k = *S.k, ld = S.m + 1;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         rhs[i] = S.g[i];
@@ -798,9 +805,37 @@ static die_status k_update_defl(const double2* V, long ldv, int k, const double2
     return DIE_OK;
 }
 
+// Projections h = V^* w over a basis of any length, in chunks of kBasisChunk vectors
+// (every chunk projects the same w); with_norm: ||w||^2 lands at h[nv].
+static die_status dots_chunked(const double2* V, long ldv, int nv, const double2* w, long n, int with_norm,
+                               double2* h, const RedScratch& rs, const int* skip, cudaStream_t st, bool live,
+                               const double* VM) {
+    for (int a = 0; a < nv; a += kBasisChunk) {
+        const int cnt = nv - a < kBasisChunk ? nv - a : kBasisChunk;
+        const bool last = a + cnt >= nv;
+        DIE_TRY(k_dots(V + (long)a * ldv, ldv, cnt, w, n, last ? with_norm : 0, h + a, rs, skip, st, live,
+                       VM ? VM + (long)a * ldv : nullptr));
+    }
+    return DIE_OK;
+}
+
+// w -= V h over a basis of any length: the chunks before the last subtract without a norm,
+// the last one runs `last_update` (the norm, the DGKS decision, folded projections).
+template <typename F>
+static die_status update_chunked(const double2* V, long ldv, int nv, const double2* h, double2* w, long n,
+                                 const RedScratch& rs, const int* skip, cudaStream_t st, const double* VM,
+                                 F&& last_update) {
+    int a = 0;
+    for (; nv - a > kBasisChunk; a += kBasisChunk)
+        DIE_TRY(k_basis_axpy(V + (long)a * ldv, ldv, kBasisChunk, h + a, -1.0, w, w, n, nullptr, nullptr, rs, skip,
+                             st, false, VM ? VM + (long)a * ldv : nullptr));
+    return last_update(V + (long)a * ldv, nv - a, h + a, VM ? VM + (long)a * ldv : nullptr);
+}
+
 die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, double2* h1, double2* h2, double2* nrm,
                     int* reorth, int* skip2, const int* done, double eta2, const RedScratch& rs, cudaStream_t st,
                     double* inv, const DeflProj* dp, double* VM, int* abort_flags, int* abort_done) {
+    if (nv < 1 || nv > kMaxRestart + 1) return DIE_EINVAL;
     Dgks dec;
     dec.before2 = h1 + nv;
     dec.reorth = reorth;
@@ -811,21 +846,43 @@ die_status cgs_dgks(const double2* V, long ldv, int nv, double2* w, long n, doub
     dec.eta2 = eta2;
     dec.abort_flags = abort_flags;
     dec.abort_done = abort_done;
-    DIE_TRY(k_dots(V, ldv, nv, w, n, 1, h1, rs, done, st, true, VM));
-    if (dp) DIE_TRY(k_update_defl(V, ldv, nv, h1, w, n, nrm, dec, 1, *dp, rs, done, st, true, VM));
-    else DIE_TRY(k_basis_axpy(V, ldv, nv, h1, -1.0, w, w, n, nrm, &dec, rs, done, st, true, VM));
+    DIE_TRY(dots_chunked(V, ldv, nv, w, n, 1, h1, rs, done, st, true, VM));
+    DIE_TRY(update_chunked(V, ldv, nv, h1, w, n, rs, done, st, VM,
+                           [&](const double2* Vl, int cnt, const double2* hl, const double* VMl) {
+                               return dp ? k_update_defl(Vl, ldv, cnt, hl, w, n, nrm, dec, 1, *dp, rs, done, st, true,
+                                                         VMl)
+                                         : k_basis_axpy(Vl, ldv, cnt, hl, -1.0, w, w, n, nrm, &dec, rs, done, st,
+                                                        true, VMl);
+                           }));
     if (abort_flags) return DIE_OK;   // single-pass cycle: no second-pass launches
     Dgks last;                       // second pass: no decision, only the scale factor
     last.inv = inv;
     g_prof_override = PK_DOTS_REORTH;
-    die_status s = k_dots(V, ldv, nv, w, n, 0, h2, rs, skip2, st, false, VM);
+    die_status s = dots_chunked(V, ldv, nv, w, n, 0, h2, rs, skip2, st, false, VM);
     g_prof_override = PK_UPDATE_REORTH;
-    if (s == DIE_OK) {
-        s = dp ? k_update_defl(V, ldv, nv, h2, w, n, nrm + 1, last, 0, *dp, rs, skip2, st, false, VM)
-               : k_basis_axpy(V, ldv, nv, h2, -1.0, w, w, n, nrm + 1, &last, rs, skip2, st, false, VM);
-    }
+    if (s == DIE_OK)
+        s = update_chunked(V, ldv, nv, h2, w, n, rs, skip2, st, VM,
+                           [&](const double2* Vl, int cnt, const double2* hl, const double* VMl) {
+                               return dp ? k_update_defl(Vl, ldv, cnt, hl, w, n, nrm + 1, last, 0, *dp, rs, skip2, st,
+                                                         false, VMl)
+                                         : k_basis_axpy(Vl, ldv, cnt, hl, -1.0, w, w, n, nrm + 1, &last, rs, skip2,
+                                                        st, false, VMl);
+                           });
     g_prof_override = -1;
     return s;
+}
+
+die_status k_lincomb(const double2* V, long ldv, int k, const double2* coef, const double2* base, double2* out,
+                     long n, const RedScratch& rs, cudaStream_t st, const double* VM) {
+    if (k < 0) return DIE_EINVAL;
+    int a = 0;
+    do {        // k == 0: one launch, out = base
+        const int cnt = k - a < kBasisChunk ? k - a : kBasisChunk;
+        DIE_TRY(k_basis_axpy(V + (long)a * ldv, ldv, cnt, coef + a, 1.0, a == 0 ? base : out, out, n, nullptr,
+                             nullptr, rs, nullptr, st, false, VM ? VM + (long)a * ldv : nullptr));
+        a += cnt;
+    } while (a < k);
+    return DIE_OK;
 }
 
 die_status k_scale_inv_sqrt(double2* v, long n, const double2* nrm2, const int* skip, cudaStream_t st, float2* v32,
@@ -850,8 +907,21 @@ die_status k_to_c64(const double2* x, float2* y, long n, cudaStream_t st) {
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
+static size_t finish_smem_bytes(int j) { return (size_t)(3 * j + 2) * sizeof(double2); }
+static size_t lsq_smem_bytes(int m) { return (size_t)2 * m * sizeof(double2); }
+
+die_status krylov_prepare(int m) {
+    if (m < 1 || m > kMaxRestart) return DIE_EINVAL;
+    DIE_CUDA_TRY(cudaFuncSetAttribute(arnoldi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)finish_smem_bytes(kMaxRestart)));
+    DIE_CUDA_TRY(cudaFuncSetAttribute(gmres_lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lsq_smem_bytes(kMaxRestart)));
+    return DIE_OK;
+}
+
 die_status k_arnoldi_finish(GmresDev S, int j, cudaStream_t st) {
-    DIE_PROF(PK_GIVENS, st, arnoldi_finish_kernel<<<1, 128, 0, st>>>(S, j));
+    if (j < 0 || j >= kMaxRestart) return DIE_EINVAL;
+    DIE_PROF(PK_GIVENS, st, arnoldi_finish_kernel<<<1, 128, finish_smem_bytes(j), st>>>(S, j));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -861,7 +931,8 @@ die_status k_cycle_scalars(GmresDev S, double bnorm, int step0, cudaStream_t st)
     return DIE_OK;
 }
 die_status k_gmres_lsq(GmresDev S, cudaStream_t st) {
-    DIE_PROF(PK_SMALL, st, gmres_lsq_kernel<<<1, 64, 0, st>>>(S));
+    if (S.m < 1 || S.m > kMaxRestart) return DIE_EINVAL;
+    DIE_PROF(PK_SMALL, st, gmres_lsq_kernel<<<1, 64, lsq_smem_bytes(S.m), st>>>(S));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

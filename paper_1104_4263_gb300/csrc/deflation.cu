@@ -52,6 +52,23 @@ __global__ void rotate_basis_kernel(const double2* __restrict__ Q, long ldq, int
     }
 }
 
+// out_l = sum_i Q_i Z(i, l) for l < k (Z: p x k, column-major, ld = p), in column chunks
+// whose p x chunk block of Z fits the kernel's shared memory (so any p, k up to the
+// largest Krylov dimension run).
+static die_status rotate_basis(const double2* Q, long n, int p, const double2* Z, int k, double2* out, cudaStream_t st) {
+    constexpr size_t kSmemCap = 200 * 1024;
+    int kc = (int)(kSmemCap / ((size_t)p * sizeof(double2)));
+    if (kc < 1) return DIE_EINVAL;
+    DIE_CUDA_TRY(cudaFuncSetAttribute(rotate_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    for (int l0 = 0; l0 < k; l0 += kc) {
+        const int cnt = k - l0 < kc ? k - l0 : kc;
+        const size_t smem = (size_t)p * cnt * sizeof(double2);
+        rotate_basis_kernel<<<1216, 256, smem, st>>>(Q, n, p, Z + (long)l0 * p, p, cnt, out + (long)l0 * n, n);
+        DIE_LAUNCH_CHECK();
+    }
+    return DIE_OK;
+}
+
 // Device-side small eigenproblem of one Krylov-Schur restart (single thread, FP64).
 //   B: (p+1) x p Rayleigh matrix (column-major, ld = p+1); row p holds beta e_{p-1}.
 //   Outputs: T (p x p Schur form, |T_ii| descending, ld = p), Z (p x p, ld = p),
@@ -237,11 +254,7 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
         int kk = r + (p - r) / 2;
         if (kk >= p) kk = p - 1;
         if (kk < r) kk = r;
-        const size_t smem = (size_t)p * kk * sizeof(double2);
-        if (smem > 200 * 1024) return DIE_EINVAL;
-        DIE_CUDA_TRY(cudaFuncSetAttribute(rotate_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        rotate_basis_kernel<<<1216, 256, smem, st>>>(w.Q, n, p, w.Z, p, kk, w.Q2, n);
-        DIE_LAUNCH_CHECK();
+        DIE_TRY(rotate_basis(w.Q, n, p, w.Z, kk, w.Q2, st));
         DIE_CUDA_TRY(cudaMemcpyAsync(w.Q2 + (long)kk * n, w.Q + (long)p * n, n * sizeof(double2),
                                      cudaMemcpyDeviceToDevice, st));
         std::swap(w.Q, w.Q2);
@@ -254,17 +267,13 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     d->n = n;
     d->regularized = reg ? 1 : 0;
     d->op_id = op->id;
+    DIE_CUDA_TRY(cudaGetDevice(&d->device));
     d->id = next_handle_id();
     DIE_TRY(dalloc((void**)&d->V, (size_t)r * n * sizeof(double2)));
     DIE_TRY(dalloc((void**)&d->M, (size_t)r * r * sizeof(double2)));
     DIE_TRY(dalloc((void**)&d->s, (size_t)(r + 2) * sizeof(double2)));
     DIE_TRY(alloc_red_scratch(&d->rs));
-    {
-        const size_t smem = (size_t)p * r * sizeof(double2);
-        DIE_CUDA_TRY(cudaFuncSetAttribute(rotate_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        rotate_basis_kernel<<<1216, 256, smem, st>>>(w.Q, n, p, w.Z, p, r, d->V, n);
-        DIE_LAUNCH_CHECK();
-    }
+    DIE_TRY(rotate_basis(w.Q, n, p, w.Z, r, d->V, st));
     // re-orthonormalise V (CGS2) so that V^* V = I to FP64 accuracy
     for (int j = 0; j < r; j++) {
         double2* vj = d->V + (long)j * n;

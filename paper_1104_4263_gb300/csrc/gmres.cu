@@ -3,8 +3,8 @@
 //
 // One cycle runs entirely on the device without host round trips.  Each Arnoldi
 // vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion: a second
-// pass only when the first left less than eta of ||w|| (eta = 0.01 unless the caller
-// sets it).  Cycles start single-pass (the second-pass kernels are not launched); a
+// pass only when the first left less than eta of ||w|| (eta = 1/sqrt(2), the classical
+// choice, unless the caller sets it).  Cycles start single-pass (the second-pass kernels are not launched); a
 // cycle in which the criterion fires stops and runs again with the second passes, and
 // the solve keeps them.  The passes use the three-multiplication form of the complex
 // products (Re - Im of every basis vector is stored when the vector is normalised).
@@ -131,6 +131,7 @@ static die_status init_cache(SolverCache* c, dieop_s* op, int m, int hist_cap, b
     }
     DIE_TRY(alloc_red_scratch(&c->rs));
     DIE_TRY(alloc_red_scratch(&c->ds.rs));
+    DIE_TRY(krylov_prepare(m));
     const double2 one = make_double2(1.0, 0.0);
     DIE_CUDA_TRY(cudaMemcpy(c->one, &one, sizeof one, cudaMemcpyHostToDevice));
     DIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -138,12 +139,20 @@ static die_status init_cache(SolverCache* c, dieop_s* op, int m, int hist_cap, b
     for (auto& e : c->join) DIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     DIE_CUDA_TRY(cudaEventCreateWithFlags(&c->back, cudaEventDisableTiming));
+    return DIE_OK;      // the timing events (gmres_opts.timing) are created on first use
+}
+
+// Timing events of gmres_opts.timing: four per Arnoldi step of a cycle.
+static die_status ensure_events(SolverCache* c) {
+    const size_t need = 4 * (size_t)(c->m_cap + 1);
+    if (c->ev.size() >= need) return DIE_OK;
+    const size_t have = c->ev.size();
     try {
-        c->ev.resize(4 * (size_t)(m + 1));       // null handles until created
+        c->ev.resize(need);       // null handles until created
     } catch (...) {
         return DIE_ENOMEM;
     }
-    for (auto& e : c->ev) DIE_CUDA_TRY(cudaEventCreate(&e));
+    for (size_t i = have; i < need; i++) DIE_CUDA_TRY(cudaEventCreate(&c->ev[i]));
     return DIE_OK;
 }
 
@@ -274,7 +283,7 @@ static double seconds_since(std::chrono::steady_clock::time_point t0) {
 using namespace die;
 
 static bool opts_valid(const dieop_s* op, const defl_s* defl, const gmres_opts* o) {
-    if (o->restart < 1 || o->restart > 256 || o->max_iters < 0 || !(o->tol >= 0)) return false;
+    if (o->restart < 1 || o->restart > kMaxRestart || o->max_iters < 0 || !(o->tol >= 0)) return false;
     if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return false;
     if (defl && (defl->op_id != op->id || defl->regularized != (o->regularized ? 1 : 0))) return false;
     return true;
@@ -334,7 +343,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
                             gmres_report* rep, cudaStream_t ust, SolverCache* c, bool pin) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
-    const double eta = o->reorth_eta > 0 ? o->reorth_eta : 0.01;
+    const double eta = o->reorth_eta > 0 ? o->reorth_eta : kDefaultReorthEta;
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
     const int m = o->restart;
     const long n = 2L * op->N;
@@ -384,6 +393,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
     S.hist_cap = c->hist_cap;
     S.tol = o->tol;
     DIE_CUDA_TRY(cudaMemsetAsync(c->ints, 0, ints_count(m) * sizeof(int), st));
+    if (o->timing) DIE_TRY(ensure_events(c));
 
     // right-hand side of the solved system
     const double2* bt = b;
@@ -571,12 +581,11 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         if (k == 0) { status = DIE_EBREAKDOWN; break; }
         DIE_TRY(k_gmres_lsq(S, st));
         if (defl) {
-            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, nullptr, c->tmp, n, nullptr, nullptr, c->rs, nullptr, st, false,
-                                 Vm));
+            DIE_TRY(k_lincomb(V, ldv, k, S.y, nullptr, c->tmp, n, c->rs, st, Vm));
             DIE_TRY(defl_apply(defl, c->tmp, c->tmp, nullptr, st, false, &c->ds));
             DIE_TRY(k_basis_axpy(c->tmp, ldv, 1, c->one, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st));
         } else {
-            DIE_TRY(k_basis_axpy(V, ldv, k, S.y, 1.0, x, x, n, nullptr, nullptr, c->rs, nullptr, st, false, Vm));
+            DIE_TRY(k_lincomb(V, ldv, k, S.y, x, x, n, c->rs, st, Vm));
         }
         // a singular triangular factor (breakdown with no exact solution) shows up after the LSQ
         DIE_CUDA_TRY(cudaMemcpyAsync(c->host, c->ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -617,6 +626,15 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
         }
     }
     return status;
+}
+
+extern "C" die_status gmres_basis(dieop_t op, int first, int count, void* out, void* stream) {
+    if (!op || !out || first < 0 || count < 1) return DIE_EINVAL;
+    SolverCache* c = solver_cache(op);
+    if (!c || (long)first + count > (long)c->m_cap + 1) return DIE_EINVAL;
+    DIE_CUDA_TRY(cudaMemcpyAsync(out, c->V + (long)first * c->n, (size_t)count * c->n * sizeof(double2),
+                                 cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return DIE_OK;
 }
 
 extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, const void* b_, void* x_,

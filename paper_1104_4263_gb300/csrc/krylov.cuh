@@ -15,8 +15,15 @@ constexpr int kRedBlocks = 304;      // 2 blocks per SM on a 152-SM GB300; fixed
 constexpr int kRedThreads = 256;
 constexpr int kRedGroup = 16;        // blocks per first-level group of the final sums
 constexpr int kRedGroups = kRedBlocks / kRedGroup;
-constexpr int kMaxBasis = 320;       // largest basis a single call handles
+constexpr int kMaxBasis = 320;       // largest basis a single projection / update launch handles
+constexpr int kBasisChunk = 256;     // longer bases are swept in chunks of this many vectors
+constexpr int kMaxRestart = 2048;    // largest GMRES restart (Krylov dimension per cycle)
+// Default DGKS threshold: a second classical Gram-Schmidt pass when the first left
+// ||w'|| < eta ||w||.  1/sqrt(2) keeps the basis orthonormal to working precision for any
+// cycle length; a looser eta (fewer second passes) loses orthogonality as cycles grow.
+constexpr double kDefaultReorthEta = 0.70710678118654752440;
 static_assert(kRedBlocks % kRedGroup == 0, "reduction groups must tile the grid");
+static_assert(kBasisChunk + 1 <= kMaxBasis, "a chunk and the norm fit the reduction scratch");
 
 // Reduction scratch.  Each block writes one partial per vector ([vector][block]); the
 // last block of each group of kRedGroup consecutive blocks to arrive sums the group's
@@ -144,6 +151,13 @@ die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, 
 die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, const double* inv, long n,
                     double2* out, const float2* M32, float2* cf, const RedScratch& rs, const int* skip,
                     cudaStream_t st, bool live = false);
+// out = base + sum_i V_i coef_i for any k (chunks of kBasisChunk vectors; base may be NULL
+// = 0, out may equal base); no norm, no skip flag.  VM as for k_basis_axpy.
+die_status k_lincomb(const double2* V, long ldv, int k, const double2* coef, const double2* base, double2* out,
+                     long n, const RedScratch& rs, cudaStream_t st, const double* VM = nullptr);
+// Sets the dynamic shared-memory limits of the per-step GMRES kernels for restarts up to
+// m (call once per device, outside any stream capture, before the first solve).
+die_status krylov_prepare(int m);
 // out = base + sign * sum_i V_i c_i (base may be NULL = 0, out may equal base), c = coef.
 // nrm2 != NULL: ||out||^2 into nrm2[0] (device), and the DGKS decision if dec != NULL.
 // VM != NULL: the three-multiplication form, with Re - Im of every V_i in VM.
@@ -161,7 +175,9 @@ die_status k_defl_update32(const float2* V, long ldv, int r, const float2* cf, c
                            double* wm = nullptr);
 
 // Classical Gram-Schmidt of w against V_0..V_{nv-1} with the DGKS criterion (done is a
-// live flag, see above):
+// live flag, see above); any nv up to kMaxRestart + 1 (bases longer than kBasisChunk
+// are swept in chunks: the projections of all chunks use the same w, as classical
+// Gram-Schmidt requires, and the update subtracts chunk after chunk):
 // h1 = V^* w (||w||^2 in h1[nv]); w -= V h1 (||w||^2 -> nrm[0]); if ||w||^2 < eta2
 // ||w_before||^2 (always when eta2 >= 1): h2 = V^* w; w -= V h2 (||w||^2 -> nrm[1]).
 // inv != NULL receives 1 / ||w|| of the final w (1 if that norm is zero or not finite).

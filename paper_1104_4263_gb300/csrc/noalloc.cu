@@ -25,10 +25,9 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
 static std::mutex g_noalloc_mu;
 static double2* g_noalloc_addr[kNoAllocMaxDevices];
 
-// Device address of the array on the current device (looked up once per device).
-static die_status noalloc_scratch(double2** out) {
-    int dev = 0;
-    DIE_CUDA_TRY(cudaGetDevice(&dev));
+// Device address of the array on device `dev`, the current one (looked up once per
+// device and kept; a cudaDeviceReset makes the kept address stale).
+static die_status noalloc_scratch(int dev, double2** out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return DIE_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
@@ -51,8 +50,11 @@ using namespace die;
 extern "C" die_status deflation_apply_noalloc(defl_t d, const void* x, void* z, void* stream) {
     if (!d || !x || !z) return DIE_EINVAL;
     if (d->r < 1 || d->r > kNoAllocMaxR) return DIE_EINVAL;
+    int dev = 0;
+    DIE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != d->device) return DIE_EINVAL;      // V and M live on another device
     double2* base = nullptr;
-    DIE_TRY(noalloc_scratch(&base));
+    DIE_TRY(noalloc_scratch(dev, &base));
     cudaStream_t st = (cudaStream_t)stream;
     RedScratch rs;
     rs.partial = base;

@@ -82,6 +82,7 @@ void free_red_scratch(RedScratch* rs);
 struct defl_s {
     uint64_t id = 0;            // unique identity of this handle
     uint64_t op_id = 0;
+    int device = -1;            // CUDA device the handle's arrays live on
     int r = 0;
     long n = 0;
     int regularized = 0;

@@ -54,6 +54,11 @@ class DeflOpts(ct.Structure):
                 ("seed", ct.c_ulonglong)]
 
 
+class FnoDesc(ct.Structure):
+    _fields_ = [("c_in", ct.c_int), ("c_out", ct.c_int), ("width", ct.c_int), ("modes", ct.c_int),
+                ("layers", ct.c_int), ("hidden", ct.c_int), ("H", ct.c_int), ("W", ct.c_int), ("max_batch", ct.c_int)]
+
+
 ABI_VERSION = 2
 STRUCTS = (Desc, GmresOpts, GmresReport, DeflOpts)     # the order of die_abi_sizes
 
@@ -69,6 +74,7 @@ EXPORTS = {
     "dieop_destroy": (None, [ct.c_void_p]),
     "gmres_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p, ct.c_void_p,
                                ct.POINTER(GmresReport), ct.c_void_p]),
+    "gmres_basis": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
     "gmres_solve_batch": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_int, ct.c_void_p,
                                      ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "gmres_solve_many": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_void_p,
@@ -85,6 +91,24 @@ EXPORTS = {
     "die_prof_name": (ct.c_char_p, [ct.c_int]),
     "die_prof_read": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_double)]),
     "die_status_str": (ct.c_char_p, [ct.c_int]),
+    "die_gemm_bf16": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_float, ct.c_void_p, ct.c_longlong,
+                                 ct.c_longlong, ct.c_longlong, ct.c_void_p, ct.c_longlong, ct.c_longlong,
+                                 ct.c_longlong, ct.c_float, ct.c_void_p, ct.c_longlong, ct.c_longlong,
+                                 ct.c_longlong, ct.c_int, ct.c_void_p]),
+    "fno_create": (ct.c_int, [ct.POINTER(FnoDesc), ct.POINTER(ct.c_void_p)]),
+    "fno_destroy": (None, [ct.c_void_p]),
+    "fno_param_count": (ct.c_longlong, [ct.c_void_p]),
+    "fno_set_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "fno_get_params": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "fno_forward": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "fno_backward": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "fno_zero_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "fno_get_grads": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "fno_train_step": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_float,
+                                  ct.POINTER(ct.c_float), ct.c_void_p]),
+    "fno_precondition": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "fgmres_solve": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.POINTER(GmresOpts), ct.c_int, ct.c_int,
+                                ct.c_void_p, ct.c_void_p, ct.POINTER(GmresReport), ct.POINTER(ct.c_int), ct.c_void_p]),
     "die_abi_version": (ct.c_int, []),
     "die_abi_sizes": (ct.c_int, [ct.POINTER(ct.c_longlong), ct.c_int]),
 }
@@ -295,6 +319,14 @@ class Operator:
             out["history"] = hist[:rep.history_len].copy()
         return x, out
 
+    def basis(self, first: int, count: int, stream=None):
+        """Vectors first .. first + count - 1 of the Krylov basis the last gmres_solve on
+        this operator left (complex128, shape (count, 2, n2, n1)); see gmres_basis."""
+        import torch
+        out = torch.empty((count, 2, self.n2, self.n1), dtype=torch.complex128, device="cuda")
+        _check(_lib().gmres_basis(self._h, int(first), int(count), _ptr(out), _stream(stream)), "gmres_basis")
+        return out
+
     def solve_batch(self, B, X=None, restart: int = 30, tol: float = 1e-6, max_iters: int = 100000,
                     regularized: bool = False, inner: int = DIE_FP64, deflation: "Deflation | None" = None,
                     stream=None, reorth_eta: float = 0.0, graph: bool = False):
@@ -403,3 +435,126 @@ def solve_many(ops, bs, deflations=None, xs=None, restart: int = 30, tol: float 
              "n_apply": r.n_apply, "rel_res_solved": r.rel_res_solved, "rel_res_orig": r.rel_res_orig,
              "t_total": r.t_total, "n_reorth": r.n_reorth, "graph_cycles": r.graph_cycles} for r in reps]
     return xs, outs
+
+
+def gemm_bf16(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, stream=None):
+    """C = alpha A B^T + beta C on the tensor cores (BF16 operands, FP32 accumulation), for
+    float32 CUDA tensors A (M x K) and B (N x K) of any strides (or batched, 3-D)."""
+    import torch
+    if A.dtype != torch.float32 or B.dtype != torch.float32 or not A.is_cuda or not B.is_cuda:
+        raise TypeError("gemm_bf16 takes float32 CUDA tensors")
+    batched = A.dim() == 3
+    A3 = A if batched else A.unsqueeze(0)
+    B3 = B if batched else B.unsqueeze(0)
+    bt, M, K = A3.shape
+    N = B3.shape[1]
+    if B3.shape[2] != K or B3.shape[0] != bt:
+        raise ValueError("shapes do not match")
+    if C is None:
+        C = torch.zeros((bt, M, N) if batched else (M, N), dtype=torch.float32, device=A.device)
+    C3 = C if batched else C.unsqueeze(0)
+    sa, sb, sc = A3.stride(), B3.stride(), C3.stride()
+    _check(_lib().die_gemm_bf16(M, N, K, bt, float(alpha), ct.c_void_p(A3.data_ptr()), sa[1], sa[2], sa[0],
+                                ct.c_void_p(B3.data_ptr()), sb[1], sb[2], sb[0], float(beta),
+                                ct.c_void_p(C3.data_ptr()), sc[1], sc[2], sc[0], 1, _stream(stream)), "die_gemm_bf16")
+    return C
+
+
+class FNO:
+    """Fourier neural operator on the tensor cores (an fno_t handle); see include/die_fno.h."""
+
+    def __init__(self, c_in=6, c_out=4, width=32, modes=16, layers=4, hidden=128, H=128, W=128, max_batch=16):
+        self.desc = FnoDesc(c_in, c_out, width, modes, layers, hidden, H, W, max_batch)
+        h = ct.c_void_p()
+        _check(_lib().fno_create(ct.byref(self.desc), ct.byref(h)), "fno_create")
+        self._h = h
+        self.n_params = int(_lib().fno_param_count(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {a.size}")
+        _check(_lib().fno_set_params(self._h, a.ctypes.data_as(ct.c_void_p)), "fno_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib().fno_get_params(self._h, a.ctypes.data_as(ct.c_void_p)), "fno_get_params")
+        return a
+
+    def get_grads(self):
+        import numpy as np
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib().fno_get_grads(self._h, a.ctypes.data_as(ct.c_void_p)), "fno_get_grads")
+        return a
+
+    def zero_grads(self, stream=None):
+        _check(_lib().fno_zero_grads(self._h, _stream(stream)), "fno_zero_grads")
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        d = self.desc
+        if x.dtype != torch.float32 or x.dim() != 4 or tuple(x.shape[1:]) != (d.c_in, d.H, d.W):
+            raise ValueError("x must be float32 (batch, c_in, H, W)")
+        y = torch.empty((x.shape[0], d.c_out, d.H, d.W), dtype=torch.float32, device=x.device) if y is None else y
+        _check(_lib().fno_forward(self._h, x.shape[0], _ptr(x), _ptr(y), _stream(stream)), "fno_forward")
+        return y
+
+    def backward(self, gy, want_gx: bool = False, stream=None):
+        import torch
+        d = self.desc
+        gx = torch.empty((gy.shape[0], d.c_in, d.H, d.W), dtype=torch.float32, device=gy.device) if want_gx else None
+        _check(_lib().fno_backward(self._h, gy.shape[0], _ptr(gy), _ptr(gx) if gx is not None else None,
+                                   _stream(stream)), "fno_backward")
+        return gx
+
+    def train_step(self, x, t, lr: float, stream=None) -> float:
+        loss = ct.c_float()
+        _check(_lib().fno_train_step(self._h, x.shape[0], _ptr(x), _ptr(t), float(lr), ct.byref(loss),
+                                     _stream(stream)), "fno_train_step")
+        return float(loss.value)
+
+    def precondition(self, op: "Operator", v, z=None, stream=None):
+        import torch
+        z = torch.empty_like(v) if z is None else z
+        _check(_lib().fno_precondition(self._h, op.handle, _ptr(v), _ptr(z), _stream(stream)), "fno_precondition")
+        return z
+
+
+def fgmres(op: "Operator", b, net: "FNO | None" = None, deflation: "Deflation | None" = None, x=None,
+           restart: int = 30, tol: float = 1e-6, max_iters: int = 300, fallback_restart: int = 30,
+           fallback_iters: int = 0, reorth_eta: float = 0.0, stream=None):
+    """Flexible GMRES with the network as initial guess and right preconditioner (fgmres_solve);
+    returns (x, report dict)."""
+    import torch
+    if b.dtype != torch.complex128:
+        raise TypeError("fgmres takes complex128 vectors")
+    use_x0 = x is not None
+    x = torch.empty_like(b) if x is None else x
+    opts = GmresOpts(restart, max_iters, tol, 0, int(use_x0), DIE_FP64, 0, float(reorth_eta), 0)
+    rep = GmresReport()
+    used = ct.c_int(0)
+    code = _lib().fgmres_solve(op.handle, net.handle if net is not None else None,
+                               deflation.handle if deflation is not None else None, ct.byref(opts),
+                               fallback_restart, fallback_iters, _ptr(b), _ptr(x), ct.byref(rep), ct.byref(used),
+                               _stream(stream))
+    if code not in (0, 5):
+        raise DieError(code, "fgmres_solve")
+    return x, {"status": STATUS[code], "converged": code == 0, "cycles": rep.cycles, "iters": rep.iters,
+               "rel_res_orig": rep.rel_res_orig, "used_fallback": bool(used.value)}

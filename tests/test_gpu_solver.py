@@ -46,9 +46,10 @@ def test_plain_gmres_config1(cyl32):
     assert abs(rep["iters"] - ref.iters) <= 0.1 * ref.iters, (rep["iters"], ref.iters)
 
 
-@pytest.mark.parametrize("eta", [0.0, 0.1, 1.0])
+@pytest.mark.parametrize("eta", [0.0, 0.01, 1.0])
 def test_reorth_threshold_keeps_solution(cyl32, eta):
-    """Default (0.01), looser and always-on re-orthogonalisation all reach the direct solution."""
+    """Default (1/sqrt(2)), looser (0.01) and always-on re-orthogonalisation all reach the
+    direct solution."""
     p, A, b, x = cyl32
     op = die.Operator(p.eps_r, p.h)
     u, rep = op.solve(op.plane_wave(0.0), restart=20, tol=1e-8, max_iters=20000, reorth_eta=eta)
@@ -291,3 +292,85 @@ def test_solve_many_equals_single_solves():
         assert reps[k]["iters"] == rk["iters"]
         assert torch.equal(xs[k], xk)
         assert reps[k]["converged"]
+
+
+def test_fp64_solution_gate_config1(cyl32):
+    """The FP64 gate: the 32^2 cylinder solved to 1e-13 by the GPU's GMRES(20) and by the
+    oracle (its GMRES, and the direct solve); the solutions agree to 1e-10 relative."""
+    p, A, b, x = cyl32
+    op = die.Operator(p.eps_r, p.h)
+    u, rep = op.solve(op.plane_wave(0.0), restart=20, tol=1e-13, max_iters=40000)
+    assert rep["converged"] and rep["rel_res_solved"] <= 1e-13, rep
+    ug = u.cpu().numpy()
+    assert rel(ug, x) < 1e-10
+    ref = gmres.gmres(lambda v: dense.matvec(A, v), b, 20, 1e-13, 40000)
+    assert ref.converged
+    assert rel(ug, ref.x) < 1e-10
+    # element by element as well
+    assert np.max(np.abs(ug - x)) / np.max(np.abs(x)) < 1e-10
+
+
+def _orthogonality(op, first, count):
+    """max |V* V - I| over basis vectors first .. first + count - 1 (on the GPU, torch)."""
+    V = op.basis(first, count).reshape(count, -1)
+    G = V.conj() @ V.transpose(0, 1)
+    return float((G - torch.eye(count, dtype=G.dtype, device=G.device)).abs().max())
+
+
+@pytest.mark.parametrize("restart,inner,defl_r", [(30, die.DIE_FP32_INNER, 20), (30, die.DIE_FP64, 0),
+                                                  (300, die.DIE_FP32_INNER, 20)])
+def test_basis_orthogonality_512(restart, inner, defl_r):
+    """One full cycle on the 512^2 core-shell at the default re-orthogonalisation threshold:
+    the Arnoldi vectors v_1 .. v_{m-1} the cycle leaves are orthonormal to 1e-8 (max entry of
+    V* V - I), also across the chunk boundary of a 300-vector basis."""
+    p = W.config2(512)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    D = die.Deflation(op, defl_r, tol=1e-4, regularized=True, inner=inner) if defl_r else None
+    _, rep = op.solve(b, restart=restart, tol=1e-12, max_iters=restart, regularized=True, inner=inner, deflation=D)
+    assert rep["iters"] == restart and rep["cycles"] == 1
+    loss = _orthogonality(op, 1, restart - 1)
+    assert loss < 1e-8, loss
+
+
+def test_large_restart_first_cycle_matches_oracle():
+    """GMRES(300) (a basis longer than one 256-vector chunk) on the regularised core-shell
+    operator at 64^2: the first cycle's residual estimates equal the oracle's GMRES(300)
+    (same Krylov space) to 1e-7 relative, and the final residuals agree."""
+    p = W.config2(64)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    _, rep = op.solve(b, restart=300, tol=1e-12, max_iters=300, regularized=True, history=300)
+    ref = fftmv.FFTOperator(p.eps_r, p.h)
+    bh = b.cpu().numpy()
+    res = gmres.gmres(ref.apply_regularized, ref.apply_R(bh), 300, 1e-12, 300)
+    h, hr = rep["history"], np.array(res.history)
+    assert len(h) == 300 and len(hr) == 300
+    assert np.max(np.abs(h - hr) / hr) < 1e-7
+    assert abs(rep["rel_res_solved"] - res.rel_res) <= 1e-6 * res.rel_res
+
+
+def test_core_shell_plateau_matches_oracle():
+    """The stagnation of restarted GMRES on the core-shell object is the method's, not the
+    solver's: at the bench's resolution (h = 1/64) on a 128^2 grid, GPU and oracle run
+    A_R A P^-1 with GMRES(30) for 300 steps, each with its own deflation of the r = 5
+    largest-magnitude eigenvalues (Krylov-Schur on the GPU; ARPACK eigs and modified
+    Gram-Schmidt in the oracle, as Section 5 does; r = 5 sits at a gap of the spectrum,
+    |lambda_5| = 22.0 > |lambda_6| = 15.7, so the deflated subspace is well defined).  The
+    first cycle's estimates agree to 1e-6, and both stall at the same residual (within 5%)."""
+    p = W.config2(128)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    D = die.Deflation(op, 5, tol=1e-10, regularized=True)
+    assert D.converged
+    _, rep = op.solve(b, restart=30, tol=1e-12, max_iters=300, regularized=True, deflation=D, history=300)
+    ref = fftmv.FFTOperator(p.eps_r, p.h, workers=8)
+    Dref = deflation.Deflation.from_operator(ref.apply_regularized, (2, 128, 128), 5, tol=1e-10)
+    assert np.max(np.abs(np.sort(np.abs(D.eigenvalues)) - np.sort(np.abs(Dref.eigs)))) < 1e-6 * abs(Dref.eigs[0])
+    bh = b.cpu().numpy()
+    res = gmres.gmres(ref.apply_regularized, ref.apply_R(bh), 30, 1e-12, 300, precond=Dref.apply)
+    h, hr = rep["history"], np.array(res.history)
+    assert len(h) == 300 and len(hr) == 300
+    assert np.max(np.abs(h[:30] - hr[:30]) / hr[:30]) < 1e-6
+    assert abs(h[-1] - hr[-1]) <= 0.05 * hr[-1], (h[-1], hr[-1])
+    assert hr[-1] > 1e-2 and hr[-1] > 0.7 * hr[149]        # the plateau: no progress in the last half
