@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define DIE_ABI_VERSION 2
+#define DIE_ABI_VERSION 3
 
 typedef enum die_status {
     DIE_OK = 0,
@@ -57,6 +57,20 @@ typedef enum die_precision {
     DIE_FP32_INNER = 1     /* complex64 FFT products; FP64 for everything else                */
 } die_precision;
 
+/* Polarisation (Section 2).  DIE_TE: the unknowns (E1, E2) of Eq. (2.15) with the
+ * Green's tensor of Eqs. (4.3)-(4.5).  DIE_TM: the scalar E-wave unknown E3 of Eq. (2.16),
+ * E3_in = E3 - k_b^2 g * (chi E3), on the same grid with the scalar kernel
+ * k_b^2 h^2 (i/4) H0(k_b r) and, on the diagonal, the integral of k_b^2 g over the
+ * equal-area disc of Eq. (4.4), (i pi/2) k_b a H1(k_b a) - 1.  A TM field vector keeps the
+ * two-plane layout below with E3 in the first plane and a zero second plane: the TM
+ * operator acts on each plane separately (the off-diagonal kernel plane is zero), so a zero
+ * second plane stays zero through every product, solve and deflation; the products cost
+ * what a TE product costs. */
+typedef enum die_polarization {
+    DIE_TE = 0,
+    DIE_TM = 1
+} die_polarization;
+
 typedef struct dieop_s* dieop_t;
 typedef struct defl_s* defl_t;
 
@@ -68,6 +82,7 @@ typedef struct dieop_desc {
     double k_b;            /* background wavenumber; <= 0 selects 2 pi                         */
     die_precision prec;    /* element type of dieop_apply / dieop_apply_regularized I/O        */
     int M1, M2;            /* FFT sizes, 0 = smallest 2^a 3^b >= 2 n; else >= 2 n and 2^a 3^b */
+    die_polarization pol;  /* DIE_TE (default, 0) or DIE_TM                                    */
 } dieop_desc;
 
 /* dieop_create -- build the operator of Eqs. (4.3)-(4.5) for a permittivity map.
@@ -80,6 +95,14 @@ typedef struct dieop_desc {
  *   DIE_ENOMEM, DIE_ECUDA.  On error *out is NULL. */
 die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_device,
                         void* stream, dieop_t* out);
+
+/* Replaces the permittivity map of an operator (same grid, h, FFT sizes: the Green
+ * spectra of Eqs. (4.3)-(4.5) do not depend on it), recomputing chi and chi'.  eps_r as
+ * for dieop_create.  On DIE_ESINGULAR (the existence condition of Eq. (3.17)) the operator
+ * keeps its previous map.  The operator gets a new identity: deflation handles built
+ * before the call are rejected by the solves.  Synchronises the stream.  Errors:
+ * DIE_EINVAL, DIE_ESINGULAR, DIE_ENOMEM, DIE_ECUDA. */
+die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_device, void* stream);
 
 /* Actual sizes chosen at create: out[0..5] = n1, n2, M1, M2, N = n1*n2, prec. */
 die_status dieop_info(dieop_t op, long long* out6);
@@ -109,7 +132,8 @@ die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* str
 die_status dieop_apply_batch(dieop_t op, int nrhs, const void* x, void* y, int regularized, void* stream);
 
 /* b = incident TE plane wave of unit |E| at angle psi to the x1 axis (Section 4, end):
- * H3 = exp(i k_b (x1 cos psi + x2 sin psi)), E1 = -sin(psi) H3, E2 = cos(psi) H3.
+ * H3 = exp(i k_b (x1 cos psi + x2 sin psi)), E1 = -sin(psi) H3, E2 = cos(psi) H3; for a
+ * TM operator E3 = exp(i k_b (x1 cos psi + x2 sin psi)) in the first plane, 0 in the second.
  * b: device, 2*n1*n2 complex128.  Errors: DIE_EINVAL, DIE_ECUDA. */
 die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream);
 
@@ -219,13 +243,14 @@ die_status gmres_solve_many(int count, const dieop_t* ops, const defl_t* defls, 
  * T = V^* Atilde V; the preconditioner is P^-1 = I + V (T^-1 - I) V^*.
  * ------------------------------------------------------------------------- */
 typedef struct defl_opts {
-    int r;                 /* eigenvalues to deflate, 1..128; 0 = count those outside the
+    int r;                 /* eigenvalues to deflate, 1..256; 0 = count those outside the
                               deflation radius of Section 5 (capped at r_max)                  */
-    int r_max;             /* cap for r = 0 (default 64 when <= 0)                             */
+    int r_max;             /* cap for r = 0 (default 64 when <= 0), <= 256                    */
     double tol;            /* Ritz residual ||Atilde y - theta y|| <= tol |theta| (1e-4)       */
     int regularized;       /* deflate A_R A (1) or A (0)                                       */
     die_precision inner;   /* precision of the products inside the eigensolver               */
-    int krylov_dim;        /* Krylov-Schur basis size; 0 = max(2 r + 16, r + 32)               */
+    int krylov_dim;        /* Krylov-Schur basis size, r + 2 .. 318; 0 = max(2 r + 16, r + 32)
+                              capped at 318                                                     */
     int max_restarts;      /* 0 = 200                                                           */
     unsigned long long seed; /* start vector seed                                              */
 } defl_opts;
@@ -247,7 +272,7 @@ die_status deflation_apply(defl_t defl, const void* x, void* z, void* stream);
  * device memory to its own pool allocator, or a latency-critical loop where the
  * device-wide synchronisation that cudaMalloc and cudaFree can cause is not
  * acceptable.  Its scratch (projections, per-block and per-group partial sums and the
- * reduction's arrival counters, about 650 KB) is a static device array inside the
+ * reduction's arrival counters, about 1.4 MB) is a static device array inside the
  * library that every GPU loading the library keeps until the process exits.
  *   - defl must have r <= 128, else DIE_EINVAL; x, z as for deflation_apply; the
  *     device current at the call must be the one defl was built on, else DIE_EINVAL.
@@ -268,6 +293,16 @@ void deflation_destroy(defl_t defl);
  * `samples` points (1000 if <= 1).  Returns a negative value on bad arguments. */
 double die_deflation_radius(const double* eps_r, long long count, int samples);
 
+/* The memory rule of Section 5 (host only): for M bytes of memory, the eigenvalue
+ * fraction beta (r = 3 N beta deflated eigenvalues), restart = x r, k_ppw points per
+ * smallest medium wavelength and the largest relative permittivity eps_max:
+ *   out3[0] = N_max = [sqrt(900 + M s) - 30] / (12 s), s = beta^2 + beta + x beta,
+ *   out3[1] = [a/lambda]_max = (sqrt(N_max) - 1) / alpha,
+ *   out3[2] = alpha = k_ppw sqrt(eps_max), so that N = (alpha a/lambda + 1)^2.
+ * (The paper's counts are for its 3N-unknown system.)  DIE_EINVAL on a NULL pointer or a
+ * non-positive input. */
+die_status die_memory_plan(double M, double beta, double x, double k_ppw, double eps_max, double* out3);
+
 /* ----------------------------------------------------------------------------
  * Kernel timing (a tracing aid; the paper has no counterpart).  Between
  * die_prof_begin and die_prof_end every kernel launch of the library is bracketed
@@ -281,6 +316,12 @@ die_status die_prof_end(void);
 int die_prof_kernels(void);                       /* number of kernel classes          */
 const char* die_prof_name(int id);                /* class name, static storage        */
 die_status die_prof_read(int id, long long* launches, double* total_ms);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (an FMA-chain kernel over
+ * every SM, best of three timed launches after a warm-up, CUDA events on `stream`): the
+ * denominator of the FP64 kernels' roofline fractions.  A measurement aid; the paper has
+ * no counterpart.  Synchronises the stream.  DIE_EINVAL on NULL, DIE_ENOMEM, DIE_ECUDA. */
+die_status die_fp64_peak(double* tflops, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* die_status_str(die_status s);

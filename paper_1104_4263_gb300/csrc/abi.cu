@@ -30,6 +30,8 @@ bool pdl_enabled() {
 
 die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st);
 die_status compute_contrasts(dieop_s* op, const double2* eps_dev, cudaStream_t st);
+die_status compute_contrasts_into(const dieop_s* op, const double2* eps_dev, double2* chi_d, double2* chir_d,
+                                  float2* chi_f, float2* chir_f, int* flag, cudaStream_t st);
 
 // Radices of a Stockham plan for L = 2^a (16 values per thread, radix <= 16) or
 // L = 3 * 2^a (12 values per thread, radix <= 4); stages balanced.
@@ -141,6 +143,7 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     op->h = desc->h;
     op->k = desc->k_b > 0 ? desc->k_b : 6.283185307179586476925286766559;
     op->prec = desc->prec;
+    op->pol = desc->pol;
     op->M1 = desc->M1 > 0 ? desc->M1 : choose_fft_size(desc->n1);
     op->M2 = desc->M2 > 0 ? desc->M2 : choose_fft_size(desc->n2);
     if (op->M1 < 2 * op->n1 || op->M2 < 2 * op->n2) return DIE_EINVAL;
@@ -209,6 +212,7 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
     if (desc->n1 < 2 || desc->n2 < 2 || desc->n1 > 2048 || desc->n2 > 2048) return DIE_EINVAL;
     if (!(desc->h > 0) || !isfinite(desc->h)) return DIE_EINVAL;
     if (desc->prec != DIE_FP64 && desc->prec != DIE_FP32_INNER) return DIE_EINVAL;
+    if (desc->pol != DIE_TE && desc->pol != DIE_TM) return DIE_EINVAL;
     dieop_s* op = new (std::nothrow) dieop_s();
     if (!op) return DIE_ENOMEM;
     die_status s;
@@ -219,6 +223,48 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
     }
     if (s != DIE_OK) { free_op(op); return s; }
     *out = op;
+    return DIE_OK;
+}
+
+die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_device, void* stream) {
+    if (!op || !eps_r) return DIE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long N = op->N;
+    // new contrasts into scratch first: the operator keeps its old ones if eps_r is rejected
+    char* scratch = nullptr;
+    const size_t cb = 2 * (size_t)N * sizeof(double2) + 2 * (size_t)N * sizeof(float2);
+    const size_t bytes = cb + (eps_on_device ? 0 : (size_t)N * sizeof(double2)) + sizeof(int);
+    if (cudaMalloc((void**)&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DIE_ENOMEM;
+    }
+    double2* cd = reinterpret_cast<double2*>(scratch);
+    double2* crd = cd + N;
+    float2* cf = reinterpret_cast<float2*>(crd + N);
+    float2* crf = cf + N;
+    const double2* e = (const double2*)eps_r;
+    if (!eps_on_device) e = reinterpret_cast<double2*>(scratch + cb);
+    int* flagd = reinterpret_cast<int*>(scratch + bytes - sizeof(int));
+    die_status s = DIE_OK;
+    int flag = 0;
+    if (!eps_on_device &&
+        cudaMemcpyAsync((void*)e, eps_r, N * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = DIE_ECUDA;
+    if (s == DIE_OK && cudaMemsetAsync(flagd, 0, sizeof(int), st) != cudaSuccess) s = DIE_ECUDA;
+    if (s == DIE_OK) s = compute_contrasts_into(op, e, cd, crd, cf, crf, flagd, st);
+    if (s == DIE_OK && (cudaMemcpyAsync(&flag, flagd, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        s = DIE_ECUDA;
+    if (s == DIE_OK && flag) s = DIE_ESINGULAR;
+    if (s == DIE_OK &&
+        (cudaMemcpyAsync(op->chi_d, cd, N * sizeof(double2), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(op->chir_d, crd, N * sizeof(double2), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(op->chi_f, cf, N * sizeof(float2), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(op->chir_f, crf, N * sizeof(float2), cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+        s = DIE_ECUDA;
+    cudaFree(scratch);           // waits for the copies
+    if (s != DIE_OK) return s;
+    op->id = next_handle_id();   // deflation handles of the old contrast no longer match
     return DIE_OK;
 }
 
@@ -290,7 +336,8 @@ die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* str
 // Incident TE plane wave (Section 4, end; component labels read so that the
 // source-free TE equations of Eq. (2.1) hold): H3 = exp(i k (x1 cos psi + x2 sin psi)),
 // E1 = -sin(psi) H3, E2 = cos(psi) H3, at cell centres x_i = (i + 1/2) h - n h / 2.
-__global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi, double2* b) {
+// TM (tm != 0): E3 = exp(i k (x1 cos psi + x2 sin psi)) in the first plane, zero in the second.
+__global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi, int tm, double2* b) {
     const long N = (long)n1 * n2;
     double sp, cp;
     sincos(psi, &sp, &cp);
@@ -300,15 +347,37 @@ __global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi
         const double x2 = (i2 + 0.5) * h - 0.5 * n2 * h;
         double s, c;
         sincos(k * (x1 * cp + x2 * sp), &s, &c);
-        b[i] = make_double2(-sp * c, -sp * s);
-        b[N + i] = make_double2(cp * c, cp * s);
+        if (tm) {
+            b[i] = make_double2(c, s);
+            b[N + i] = make_double2(0.0, 0.0);
+        } else {
+            b[i] = make_double2(-sp * c, -sp * s);
+            b[N + i] = make_double2(cp * c, cp * s);
+        }
     }
 }
 
 extern "C" die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream) {
     if (!op || !b || !isfinite(psi)) return DIE_EINVAL;
-    plane_wave_kernel<<<608, 256, 0, (cudaStream_t)stream>>>(op->n1, op->n2, op->h, op->k, psi, (double2*)b);
+    plane_wave_kernel<<<608, 256, 0, (cudaStream_t)stream>>>(op->n1, op->n2, op->h, op->k, psi,
+                                                              op->pol == DIE_TM ? 1 : 0, (double2*)b);
     DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+// Section 5's memory rule for the largest affordable grid: with alpha = k max sqrt(eps'),
+// N = alpha^2 (a/lambda)^2 + 2 alpha (a/lambda) + 1 grid points, M_A = 720 N bytes for the
+// system, M_Prec = 16 r^2 + 48 N r + 48 N restart with r = 3 N beta and restart = x r,
+// M_A + M_Prec = M gives N_max = [sqrt(900 + M s) - 30] / (12 s), s = beta^2 + beta + x beta,
+// and [a/lambda]_max = (sqrt(N_max) - 1) / alpha.
+extern "C" die_status die_memory_plan(double M, double beta, double x, double k_ppw, double eps_max, double* out3) {
+    if (!out3 || !(M > 0) || !(beta > 0) || !(x >= 0) || !(k_ppw > 0) || !(eps_max > 0)) return DIE_EINVAL;
+    const double s = beta * beta + beta + x * beta;
+    const double nmax = (sqrt(900.0 + M * s) - 30.0) / (12.0 * s);
+    const double alpha = k_ppw * sqrt(eps_max);
+    out3[0] = nmax;
+    out3[1] = (sqrt(nmax) - 1.0) / alpha;
+    out3[2] = alpha;
     return DIE_OK;
 }
 

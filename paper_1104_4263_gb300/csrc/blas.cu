@@ -729,6 +729,22 @@ __global__ void gmres_init_kernel(GmresDev S, const double2* beta2) {
 }
 
 // ------------------------------------------------------------------ launchers
+int red_blocks() {
+    static int cache[64] = {};       // per device; a benign race writes the same value
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 2 * kRedGroup; }
+    if (cache[dev]) return cache[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = kRedGroup;
+    }
+    int b = 2 * sms / kRedGroup * kRedGroup;
+    b = b < kRedGroup ? kRedGroup : (b > kRedBlocksMax ? kRedBlocksMax : b);
+    cache[dev] = b;
+    return b;
+}
+
 static inline int grid_for(long n) {
     long b = (n + kRedThreads - 1) / kRedThreads;
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
@@ -740,9 +756,9 @@ die_status k_dots(const double2* V, long ldv, int nv, const double2* w, long n, 
                   const RedScratch& rs, const int* skip, cudaStream_t st, bool live, const double* VM) {
     if (nv + 1 > kMaxBasis || nv < 0) return DIE_EINVAL;
     if (VM)
-        DIE_PROF(PK_DOTS, st, launch_pdl(proj3_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, VM, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
+        DIE_PROF(PK_DOTS, st, launch_pdl(proj3_kernel, dim3(red_blocks()), dim3(kRedThreads), 0, st, V, VM, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
     else
-        DIE_PROF(PK_DOTS, st, launch_pdl(proj_kernel<double2, kGroupFp64>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
+        DIE_PROF(PK_DOTS, st, launch_pdl(proj_kernel<double2, kGroupFp64>, dim3(red_blocks()), dim3(kRedThreads), 0, st, V, ldv, nv, w, n, with_norm, out, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -750,7 +766,7 @@ die_status k_dots32(const float2* V, long ldv, int nv, float2* x, double2* w, co
                     double2* out, const float2* M32, float2* cf, const RedScratch& rs, const int* skip,
                     cudaStream_t st, bool live) {
     if (nv > kMaxBasis || nv < 1 || (inv && !w)) return DIE_EINVAL;
-    DIE_PROF(PK_DOTS32, st, launch_pdl(proj32_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, st, V, ldv, nv, x, w, inv, n, out, M32, cf, rs, skip, live ? 1 : 0));
+    DIE_PROF(PK_DOTS32, st, launch_pdl(proj32_kernel, dim3(red_blocks()), dim3(kRedThreads), 0, st, V, ldv, nv, x, w, inv, n, out, M32, cf, rs, skip, live ? 1 : 0));
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }
@@ -761,7 +777,7 @@ die_status k_basis_axpy(const double2* V, long ldv, int k, const double2* coef, 
     const Dgks d = dec ? *dec : Dgks{};
     const int has_dec = dec && dec->reorth ? 1 : 0;
     if (nrm2) {
-        DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(basis_axpy_kernel<double2, true>, dim3(kRedBlocks), dim3(kRedThreads), 0, st,
+        DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(basis_axpy_kernel<double2, true>, dim3(red_blocks()), dim3(kRedThreads), 0, st,
                      V, ldv, k, coef, sign, (const double2*)nullptr, (const double2*)nullptr, base, out, n, nrm2, d, has_dec, rs, skip, live ? 1 : 0, VM));
     } else {
         DIE_PROF(PK_LINCOMB, st, launch_pdl(basis_axpy_kernel<double2, false>, dim3(grid_for(n)), dim3(kRedThreads), 0, st,
@@ -792,7 +808,7 @@ static die_status k_update_defl(const double2* V, long ldv, int k, const double2
                                 const int* skip, cudaStream_t st, bool live, const double* VM) {
     if (k > kMaxBasis || k < 0 || dp.r < 1 || dp.r > kDeflFoldMax) return DIE_EINVAL;
     const int ng = (dp.r + 7) / 8;
-#define UPD_CASE(NG) DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(cgs_update_defl_kernel<NG>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, \
+#define UPD_CASE(NG) DIE_PROF(PK_UPDATE_NORM, st, launch_pdl(cgs_update_defl_kernel<NG>, dim3(red_blocks()), dim3(kRedThreads), 0, st, \
                               V, ldv, k, coef, (const double2*)w, w, n, nrm2, dec, has_dec, dp, rs, skip, live ? 1 : 0, VM))
     switch (ng) {
         case 1: UPD_CASE(1); break;

@@ -173,6 +173,7 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     const bool auto_r = r == 0;
     if (auto_r) r = rmax;
     int p = o->krylov_dim > 0 ? o->krylov_dim : (2 * r + 16 > r + 32 ? 2 * r + 16 : r + 32);
+    if (o->krylov_dim <= 0 && p + 2 > kMaxBasis) p = kMaxBasis - 2;   // large r: the largest basis
     if (p <= r + 1) p = r + 2;
     if (p + 2 > kMaxBasis) return DIE_EINVAL;
     const double tol = o->tol > 0 ? o->tol : 1e-4;
@@ -202,6 +203,9 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
 
     // q_0: seeded random unit vector
     random_vector_kernel<<<1216, 256, 0, st>>>(w.Q, n, o->seed + 1);
+    // TM: a start vector in the first plane keeps the Krylov space there (the second plane
+    // of a TM field is zero), so every deflated eigenvector is a TM field
+    if (op->pol == DIE_TM) DIE_CUDA_TRY(cudaMemsetAsync(w.Q + n / 2, 0, (n / 2) * sizeof(double2), st));
     DIE_LAUNCH_CHECK();
     DIE_TRY(k_dots(w.Q, 0, 0, w.Q, n, 1, w.nrm, rs, nullptr, st));
     DIE_TRY(k_scale_inv_sqrt(w.Q, n, w.nrm, nullptr, st));
@@ -318,7 +322,8 @@ extern "C" die_status deflation_build(dieop_t op, const defl_opts* o, void* stre
     if (!out) return DIE_EINVAL;
     *out = nullptr;
     if (!op || !o) return DIE_EINVAL;
-    if (o->r < 0 || o->r > 128 || o->r_max > 128 || o->krylov_dim < 0 || o->max_restarts < 0) return DIE_EINVAL;
+    if (o->r < 0 || o->r > kMaxDeflation || o->r_max > kMaxDeflation || o->krylov_dim < 0 || o->max_restarts < 0)
+        return DIE_EINVAL;
     if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return DIE_EINVAL;
     if (o->r > 0 && 2L * op->N <= o->r + 2) return DIE_EINVAL;
     defl_s* d = new (std::nothrow) defl_s();

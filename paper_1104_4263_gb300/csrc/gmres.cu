@@ -46,12 +46,12 @@
 namespace die {
 
 die_status alloc_red_scratch(RedScratch* rs) {
-    if (cudaMalloc((void**)&rs->partial, (size_t)kMaxBasis * (kRedBlocks + kRedGroups) * sizeof(double2)) !=
+    if (cudaMalloc((void**)&rs->partial, (size_t)kMaxBasis * (kRedBlocksMax + kRedGroupsMax) * sizeof(double2)) !=
         cudaSuccess) {
         cudaGetLastError();
         return DIE_ENOMEM;
     }
-    rs->partial2 = rs->partial + (size_t)kMaxBasis * kRedBlocks;
+    rs->partial2 = rs->partial + (size_t)kMaxBasis * kRedBlocksMax;
     if (cudaMalloc((void**)&rs->counter, kRedCounters * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return DIE_ENOMEM;

@@ -28,14 +28,33 @@ __global__ void contrast_kernel(const double2* __restrict__ eps, long N, double2
 //   G11 = k^2 h^2 [P theta1^2 + Q],  G22 = k^2 h^2 [P theta2^2 + Q],  G12 = k^2 h^2 P theta1 theta2,
 //   P = (i/(2kr)) H1 - (i/4) H0,     Q = (i/4) H0 - (i/(4kr)) H1,      H_m = J_m + i Y_m.
 // Self term (Eq. (4.4)): G11 = G22 = -[1 - (i pi/4) k a H1(k a)], a = h/sqrt(pi); G12 = 0.
-__global__ void green_planes_kernel(int n1, int n2, int M1, int M2, double h, double k, double2* __restrict__ planes) {
+//
+// TM (tm != 0): the scalar kernel of the E-wave equation E3_in = E3 - k^2 g * (chi E3)
+// (Section 2) on the same grid, in both diagonal planes: G11 = G22 = k^2 h^2 (i/4) H0(k r)
+// off the diagonal, and k^2 times the integral of g over the equal-area disc on it,
+// (i pi / 2) k a H1(k a) - 1; G12 = 0, so the two planes never mix.
+__global__ void green_planes_kernel(int n1, int n2, int M1, int M2, double h, double k, int tm,
+                                    double2* __restrict__ planes) {
     const long plane = (long)M1 * M2;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < plane; idx += (long)gridDim.x * blockDim.x) {
         const int pi = (int)(idx % M1), qi = (int)(idx / M1);
         const int p = pi <= M1 / 2 ? pi : pi - M1;
         const int q = qi <= M2 / 2 ? qi : qi - M2;
         double2 g11 = make_double2(0, 0), g22 = make_double2(0, 0), g12 = make_double2(0, 0);
-        if (abs(p) < n1 && abs(q) < n2) {
+        if (tm && abs(p) < n1 && abs(q) < n2) {
+            if (p == 0 && q == 0) {
+                const double a = h * rsqrt(M_PI);
+                const double ka = k * a;
+                // (i pi/2) ka (J1 + i Y1) - 1 = (-1 - (pi/2) ka Y1) + i (pi/2) ka J1
+                g11 = make_double2(-1.0 - 0.5 * M_PI * ka * y1(ka), 0.5 * M_PI * ka * j1(ka));
+            } else {
+                const double r = h * sqrt((double)p * p + (double)q * q);
+                const double c = k * k * h * h;
+                // k^2 h^2 (i/4)(J0 + i Y0)
+                g11 = make_double2(-0.25 * c * y0(k * r), 0.25 * c * j0(k * r));
+            }
+            g22 = g11;
+        } else if (abs(p) < n1 && abs(q) < n2) {
             if (p == 0 && q == 0) {
                 const double a = h * rsqrt(M_PI);
                 const double ka = k * a;
@@ -112,7 +131,8 @@ static die_status fft_lines(double2* data, long elem_stride, long line_stride, i
 die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st) {
     const int M1 = op->M1, M2 = op->M2;
     const long plane = (long)M1 * M2;
-    green_planes_kernel<<<1216, 256, 0, st>>>(op->n1, op->n2, M1, M2, op->h, op->k, scratch);
+    green_planes_kernel<<<1216, 256, 0, st>>>(op->n1, op->n2, M1, M2, op->h, op->k, op->pol == DIE_TM ? 1 : 0,
+                                               scratch);
     DIE_LAUNCH_CHECK();
     for (int p = 0; p < 3; p++) {
         double2* base = scratch + p * plane;
@@ -124,8 +144,16 @@ die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st) 
     return DIE_OK;
 }
 
+die_status compute_contrasts_into(const dieop_s* op, const double2* eps_dev, double2* chi_d, double2* chir_d,
+                                  float2* chi_f, float2* chir_f, int* flag, cudaStream_t st);
+
 die_status compute_contrasts(dieop_s* op, const double2* eps_dev, cudaStream_t st) {
-    contrast_kernel<<<608, 256, 0, st>>>(eps_dev, op->N, op->chi_d, op->chir_d, op->chi_f, op->chir_f, op->dflag);
+    return compute_contrasts_into(op, eps_dev, op->chi_d, op->chir_d, op->chi_f, op->chir_f, op->dflag, st);
+}
+
+die_status compute_contrasts_into(const dieop_s* op, const double2* eps_dev, double2* chi_d, double2* chir_d,
+                                  float2* chi_f, float2* chir_f, int* flag, cudaStream_t st) {
+    contrast_kernel<<<608, 256, 0, st>>>(eps_dev, op->N, chi_d, chir_d, chi_f, chir_f, flag);
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -11,18 +11,23 @@
 
 namespace die {
 
-constexpr int kRedBlocks = 304;      // 2 blocks per SM on a 152-SM GB300; fixed => deterministic sums
 constexpr int kRedThreads = 256;
 constexpr int kRedGroup = 16;        // blocks per first-level group of the final sums
-constexpr int kRedGroups = kRedBlocks / kRedGroup;
+constexpr int kRedBlocksMax = 640;   // the reduction scratch holds partials of up to this many blocks
+constexpr int kRedGroupsMax = kRedBlocksMax / kRedGroup;
+// Blocks of every reduction launch: two per SM of the current device, a multiple of
+// kRedGroup (queried once per device).  The count is fixed for a device, so the
+// fixed-order sums are bitwise reproducible on it.
+int red_blocks();
 constexpr int kMaxBasis = 320;       // largest basis a single projection / update launch handles
 constexpr int kBasisChunk = 256;     // longer bases are swept in chunks of this many vectors
 constexpr int kMaxRestart = 2048;    // largest GMRES restart (Krylov dimension per cycle)
+constexpr int kMaxDeflation = 256;   // largest deflation rank (Krylov-Schur basis <= kMaxBasis - 2)
 // Default DGKS threshold: a second classical Gram-Schmidt pass when the first left
 // ||w'|| < eta ||w||.  1/sqrt(2) keeps the basis orthonormal to working precision for any
 // cycle length; a looser eta (fewer second passes) loses orthogonality as cycles grow.
 constexpr double kDefaultReorthEta = 0.70710678118654752440;
-static_assert(kRedBlocks % kRedGroup == 0, "reduction groups must tile the grid");
+static_assert(kRedBlocksMax % kRedGroup == 0, "reduction groups must tile the grid");
 static_assert(kBasisChunk + 1 <= kMaxBasis, "a chunk and the norm fit the reduction scratch");
 
 // Reduction scratch.  Each block writes one partial per vector ([vector][block]); the
@@ -31,11 +36,11 @@ static_assert(kBasisChunk + 1 <= kMaxBasis, "a chunk and the norm fit the reduct
 // group order.  The arrival counters (one per group, then the top one) are left at 0
 // by every kernel that uses them.
 struct RedScratch {
-    double2* partial = nullptr;      // kMaxBasis * kRedBlocks
-    double2* partial2 = nullptr;     // kMaxBasis * kRedGroups
+    double2* partial = nullptr;      // kMaxBasis * kRedBlocksMax
+    double2* partial2 = nullptr;     // kMaxBasis * kRedGroupsMax
     unsigned* counter = nullptr;     // kRedCounters
 };
-constexpr int kRedCounters = 1 + kRedGroups;
+constexpr int kRedCounters = 1 + kRedGroupsMax;
 
 // DGKS decision taken by the last block of a norm-computing update: reorth = always ||
 // ||w'||^2 < eta^2 ||w||^2; skip2 = done || !reorth (makes the second pass return at once).

@@ -12,13 +12,13 @@ namespace die {
 
 constexpr int kNoAllocMaxR = 128;                // largest deflation rank accepted
 constexpr int kNoAllocMaxDevices = 64;
-constexpr long kNoAllocPartials = (long)kNoAllocMaxR * kRedBlocks;
-constexpr long kNoAllocPartials2 = (long)kNoAllocMaxR * kRedGroups;
+constexpr long kNoAllocPartials = (long)kNoAllocMaxR * kRedBlocksMax;
+constexpr long kNoAllocPartials2 = (long)kNoAllocMaxR * kRedGroupsMax;
 constexpr long kNoAllocCounterSlots = (kRedCounters * sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
 // block partials | group partials | projections s | counters
 constexpr long kNoAllocSlots = kNoAllocPartials + kNoAllocPartials2 + kNoAllocMaxR + kNoAllocCounterSlots;
 
-// (128 * 304 + 128 * 19 + 128 + 5) * 16 bytes (about 650 KB), held by every GPU that
+// (128 * 640 + 128 * 40 + 128 + 11) * 16 bytes (about 1.4 MB), held by every GPU that
 // loads the library until the process exits.
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
 

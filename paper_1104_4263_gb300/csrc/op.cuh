@@ -32,6 +32,7 @@ struct dieop_s {
     int n1 = 0, n2 = 0, M1 = 0, M2 = 0, N = 0, Q1 = 0, Q2 = 0;
     double h = 0, k = 0;
     die_precision prec = DIE_FP64;
+    die_polarization pol = DIE_TE;
     die::FftPlan f1{}, i1{}, f2{}, i2{};
     double2 *tw1_d = nullptr, *tw2_d = nullptr;
     float2 *tw1_f = nullptr, *tw2_f = nullptr;

@@ -107,3 +107,56 @@ die_status die_prof_read(int id, long long* launches, double* total_ms) {
 }
 
 }  // extern "C"
+
+// FP64 throughput probe: every thread advances 8 independent chains of dependent FMAs,
+// so the FP64 pipe, not the FMA latency, bounds the kernel; the grid covers every SM.
+namespace die {
+constexpr int kProbeChains = 8;
+__global__ void fp64_probe_kernel(double* sink, int iters, double a, double b) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) x[c] = 1e-3 * (threadIdx.x + c);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; c++) x[c] = fma(x[c], a, b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) s += x[c];
+    if (s == 1234.5678) sink[blockIdx.x] = s;     // keeps the chains alive
+}
+}  // namespace die
+
+extern "C" die_status die_fp64_peak(double* tflops, void* stream) {
+    using namespace die;
+    if (!tflops) return DIE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    DIE_CUDA_TRY(cudaGetDevice(&dev));
+    DIE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 8 * sms, threads = 256, iters = 8192;
+    double* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc((void**)&sink, blocks * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return DIE_ENOMEM; }
+    die_status s = DIE_OK;
+    double best = 0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = DIE_ECUDA;
+    for (int rep = 0; s == DIE_OK && rep < 4; rep++) {     // the first run is a warm-up
+        cudaEventRecord(e0, st);
+        fp64_probe_kernel<<<blocks, threads, 0, st>>>(sink, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, st);
+        float ms = 0;
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            s = DIE_ECUDA;
+            break;
+        }
+        const double flops = 2.0 * kProbeChains * (double)iters * blocks * threads;
+        if (rep > 0 && ms > 0) best = fmax(best, flops / (ms * 1e-3) / 1e12);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    *tflops = best;
+    return s;
+}

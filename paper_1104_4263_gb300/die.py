@@ -29,9 +29,13 @@ class DieError(RuntimeError):
         super().__init__(f"{what}: {STATUS.get(code, code)} ({_lib().die_status_str(code).decode()})")
 
 
+DIE_TE = 0
+DIE_TM = 1
+
+
 class Desc(ct.Structure):
     _fields_ = [("n1", ct.c_int), ("n2", ct.c_int), ("h", ct.c_double), ("k_b", ct.c_double),
-                ("prec", ct.c_int), ("M1", ct.c_int), ("M2", ct.c_int)]
+                ("prec", ct.c_int), ("M1", ct.c_int), ("M2", ct.c_int), ("pol", ct.c_int)]
 
 
 class GmresOpts(ct.Structure):
@@ -59,13 +63,15 @@ class FnoDesc(ct.Structure):
                 ("layers", ct.c_int), ("hidden", ct.c_int), ("H", ct.c_int), ("W", ct.c_int), ("max_batch", ct.c_int)]
 
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 STRUCTS = (Desc, GmresOpts, GmresReport, DeflOpts)     # the order of die_abi_sizes
 
 
 EXPORTS = {
     "dieop_create": (ct.c_int, [ct.POINTER(Desc), ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "dieop_info": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
+    "dieop_set_permittivity": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "fno_encode_pair": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply_regularized": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply_regularizer": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -85,12 +91,15 @@ EXPORTS = {
     "deflation_apply_noalloc": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "deflation_destroy": (None, [ct.c_void_p]),
     "die_deflation_radius": (ct.c_double, [ct.c_void_p, ct.c_longlong, ct.c_int]),
+    "die_memory_plan": (ct.c_int, [ct.c_double, ct.c_double, ct.c_double, ct.c_double, ct.c_double,
+                                   ct.POINTER(ct.c_double)]),
     "die_prof_begin": (ct.c_int, []),
     "die_prof_end": (ct.c_int, []),
     "die_prof_kernels": (ct.c_int, []),
     "die_prof_name": (ct.c_char_p, [ct.c_int]),
     "die_prof_read": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_double)]),
     "die_status_str": (ct.c_char_p, [ct.c_int]),
+    "die_fp64_peak": (ct.c_int, [ct.POINTER(ct.c_double), ct.c_void_p]),
     "die_gemm_bf16": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_float, ct.c_void_p, ct.c_longlong,
                                  ct.c_longlong, ct.c_longlong, ct.c_void_p, ct.c_longlong, ct.c_longlong,
                                  ct.c_longlong, ct.c_float, ct.c_void_p, ct.c_longlong, ct.c_longlong,
@@ -167,6 +176,21 @@ def deflation_radius(eps_r) -> float:
     return float(_lib().die_deflation_radius(e.ctypes.data_as(ct.c_void_p), e.size, 1000))
 
 
+def fp64_peak_tflops(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device (die_fp64_peak), TFLOP/s."""
+    v = ct.c_double()
+    _check(_lib().die_fp64_peak(ct.byref(v), _stream(stream)), "die_fp64_peak")
+    return float(v.value)
+
+
+def memory_plan(M: float, beta: float, x: float, k_ppw: float, eps_max: float) -> dict:
+    """Section 5's memory rule (die_memory_plan): N_max, [a/lambda]_max and alpha."""
+    out = (ct.c_double * 3)()
+    _check(_lib().die_memory_plan(float(M), float(beta), float(x), float(k_ppw), float(eps_max), out),
+           "die_memory_plan")
+    return {"N_max": out[0], "a_over_lambda_max": out[1], "alpha": out[2]}
+
+
 class KernelTimer:
     """Context manager: per-kernel-class launch counts and total milliseconds
     (CUDA events around every library launch inside the block)."""
@@ -193,7 +217,7 @@ class Operator:
     """The discretised TE operator A = I - G X on an n1 x n2 grid (a dieop_t handle)."""
 
     def __init__(self, eps_r, h: float, k_b: float = 2 * math.pi, prec: int = DIE_FP64,
-                 M1: int = 0, M2: int = 0, stream=None):
+                 M1: int = 0, M2: int = 0, stream=None, pol: int = DIE_TE):
         import numpy as np
         import torch
         eps = eps_r
@@ -207,8 +231,8 @@ class Operator:
             eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128))
             n2, n1 = eps_np.shape
             on_dev = 0
-        self.n1, self.n2, self.h, self.k_b, self.prec = n1, n2, h, k_b, prec
-        desc = Desc(n1, n2, h, k_b, prec, M1, M2)
+        self.n1, self.n2, self.h, self.k_b, self.prec, self.pol = n1, n2, h, k_b, prec, pol
+        desc = Desc(n1, n2, h, k_b, prec, M1, M2, pol)
         handle = ct.c_void_p()
         ptr = _ptr(eps_t) if on_dev else eps_np.ctypes.data_as(ct.c_void_p)
         _check(_lib().dieop_create(ct.byref(desc), ptr, on_dev, _stream(stream), ct.byref(handle)), "dieop_create")
@@ -221,6 +245,23 @@ class Operator:
     @property
     def handle(self):
         return self._h
+
+    def set_permittivity(self, eps_r, stream=None):
+        """Replace the permittivity map (same grid and h; deflation handles of the old map
+        become invalid)."""
+        import numpy as np
+        import torch
+        if isinstance(eps_r, torch.Tensor) and eps_r.is_cuda:
+            e = eps_r.to(torch.complex128).contiguous()
+            if tuple(e.shape) != (self.n2, self.n1):
+                raise ValueError("eps_r must have shape (n2, n1)")
+            _check(_lib().dieop_set_permittivity(self._h, _ptr(e), 1, _stream(stream)), "dieop_set_permittivity")
+            return
+        e = np.ascontiguousarray(np.asarray(eps_r, dtype=np.complex128))
+        if e.shape != (self.n2, self.n1):
+            raise ValueError("eps_r must have shape (n2, n1)")
+        _check(_lib().dieop_set_permittivity(self._h, e.ctypes.data_as(ct.c_void_p), 0, _stream(stream)),
+               "dieop_set_permittivity")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -535,6 +576,18 @@ class FNO:
         z = torch.empty_like(v) if z is None else z
         _check(_lib().fno_precondition(self._h, op.handle, _ptr(v), _ptr(z), _stream(stream)), "fno_precondition")
         return z
+
+
+def encode_pair(op: "Operator", b, u=None, x=None, t=None, stream=None):
+    """Network input x (float32, 6 x n2 x n1) of the right-hand side b and, when u is given,
+    the target t (4 x n2 x n1) of the solution u (fno_encode_pair)."""
+    import torch
+    x = torch.empty((6, op.n2, op.n1), dtype=torch.float32, device="cuda") if x is None else x
+    if u is not None and t is None:
+        t = torch.empty((4, op.n2, op.n1), dtype=torch.float32, device="cuda")
+    _check(_lib().fno_encode_pair(op.handle, _ptr(b), _ptr(u) if u is not None else None, _ptr(x),
+                                  _ptr(t) if u is not None else None, _stream(stream)), "fno_encode_pair")
+    return x, t
 
 
 def fgmres(op: "Operator", b, net: "FNO | None" = None, deflation: "Deflation | None" = None, x=None,

@@ -135,6 +135,23 @@ def _gaussian_field(rng: np.random.Generator, n: int, h: float, corr: float) -> 
     return (g - g.mean()) / (s if s > 0 else 1.0)
 
 
+def sinusoidal(n: int = 233, a: float = 4.0) -> Problem:
+    """Section 5's continuous-permittivity object: eps_r = 10 + 5 sin(4 pi x1 / a)
+    sin(4 pi x2 / a) over the whole square domain of side a (origin at its centre), on an
+    n x n grid (233 x 233 at a = 4 wavelengths: 15 points per smallest medium wavelength)."""
+    h = a / n
+    X1, X2 = mesh(n, n, h)
+    eps_r = (10.0 + 5.0 * np.sin(4.0 * math.pi * X1 / a) * np.sin(4.0 * math.pi * X2 / a)).astype(np.complex128)
+    return Problem(f"sinusoidal a={a} n={n}", n, n, h, eps_r)
+
+
+def lossless_square(a_over_lambda: float, eps: float = 16.0, ppw: int = 15) -> Problem:
+    """Section 5's sweep object: a homogeneous lossless square filling the domain, side a,
+    at `ppw` points per medium wavelength (n = round(ppw sqrt(eps) a / lambda) + 1 cells)."""
+    n = int(round(ppw * math.sqrt(eps) * a_over_lambda)) + 1
+    return square(n, a_over_lambda / n, complex(eps))
+
+
 BATCH_SIZES = (64, 96, 128, 192, 256, 384, 512)
 
 
@@ -164,6 +181,34 @@ def config3(count: int = 64, sizes=BATCH_SIZES, h: float = 1.0 / 60.0, n_angles:
         psi = tuple(2.0 * math.pi * j / n_angles for j in range(n_angles))
         out.append(Problem(f"gaussian-ellipse #{i} n={n}", n, n, h, eps_r, psi))
     return out
+
+
+def config4_field(index: int, n: int = 128, h: float = 1.0 / 60.0, corr: float = 0.3,
+                  min_abs: float = 0.25) -> Problem:
+    """Learned-preconditioner workload: a seeded Gaussian random permittivity field over the
+    whole n x n grid, Re eps_r = -4 + 20 Phi(g1) in [-4, 16], Im eps_r = Phi(g2) in [0, 1]
+    (g1, g2 independent unit-variance fields of correlation length `corr`), values with
+    |eps_r| < min_abs pushed out to |eps_r| = min_abs (the existence condition eps != 0),
+    and a random incidence angle.  index selects the seed (training and held-out sets use
+    disjoint ranges)."""
+    rng = rng_for(4, index)
+    g1 = _gaussian_field(rng, n, h, corr)
+    g2 = _gaussian_field(rng, n, h, corr)
+    eps = (-4.0 + 20.0 * _normal_cdf(g1)) + 1j * _normal_cdf(g2)
+    a = np.abs(eps)
+    small = a < min_abs
+    eps[small] = np.where(a[small] > 0, eps[small] / np.where(a[small] > 0, a[small], 1.0) * min_abs, min_abs)
+    psi = float(rng.uniform(0.0, 2.0 * math.pi))
+    return Problem(f"random field #{index} n={n}", n, n, h, eps.astype(np.complex128), (psi,))
+
+
+def smooth_random_vector(rng: np.random.Generator, n1: int, n2: int, h: float, corr: float = 0.1) -> np.ndarray:
+    """Random complex (E1, E2) field of shape (2, n2, n1) with Gaussian correlation of length
+    `corr` (in wavelengths) and unit root-mean-square value."""
+    assert n1 == n2
+    parts = [_gaussian_field(rng, n1, h, corr) for _ in range(4)]
+    v = np.stack([parts[0] + 1j * parts[1], parts[2] + 1j * parts[3]]) / math.sqrt(2.0)
+    return v.astype(np.complex128)
 
 
 CFG5_EPS = (-6.0 + 0.5j, 2.0 + 0j, 9.0 + 0j, 30.0 + 1.0j)

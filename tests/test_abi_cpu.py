@@ -48,7 +48,7 @@ def test_binding_covers_every_symbol():
 def test_status_strings(lib):
     assert lib.die_status_str(0) == b"ok"
     assert b"singular" in lib.die_status_str(4)
-    assert lib.die_abi_version() == 2
+    assert lib.die_abi_version() == 3
 
 
 def test_struct_layouts_match_the_binding(lib):
@@ -113,3 +113,26 @@ def test_solve_many_argument_checks_without_gpu():
         die.solve_many([op], [torch.zeros(2, 4, 4, dtype=torch.complex128)])
     with pytest.raises(TypeError):            # wrong dtype
         die.solve_many([op], [torch.zeros(2, 4, 4, dtype=torch.complex64)])
+
+
+def test_memory_plan_reproduces_the_sinusoidal_example(lib):
+    """Section 5's worked example (tests/golden): 4 GB, beta 0.0011, restart 8 r, 15 points per
+    wavelength and eps up to 15 allow [a/lambda]_max = 4; at a/lambda = 4 the grid has
+    233 x 233 = 54289 points (3N = 162867), r = 3 N beta = 180 (rounded up) and the restarts
+    are 8 r and 9 r."""
+    import json
+    import math
+    from paper_1104_4263_gb300 import die
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))["memory_plan_sinusoidal"]
+    plan = die.memory_plan(g["memory_bytes"], g["beta"], g["restart_over_r"], g["points_per_wavelength"],
+                           g["eps_max"])
+    assert round(plan["a_over_lambda_max"]) == g["a_over_lambda_max"]
+    assert plan["alpha"] == pytest.approx(15 * math.sqrt(15))
+    side = round(plan["alpha"] * g["a_over_lambda_max"] + 1)      # grid points per side, 233
+    N = side * side
+    assert 3 * N == g["three_n"]
+    r = math.ceil(3 * N * g["beta"])                                # beta is "approximately 0.0011"
+    assert r == g["r"]
+    assert g["restart_over_r"] * r == g["restart_preconditioned"] and (g["restart_over_r"] + 1) * r == g["restart_original"]
+    out = (ct.c_double * 3)()
+    assert lib.die_memory_plan(-1.0, 0.1, 1.0, 15.0, 4.0, out) == 1
