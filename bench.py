@@ -293,6 +293,9 @@ def main():
     ap.add_argument("--profile-driver", action="store_true",
                     help="short fixed run for ncu captures: one complex64 regularised product, then one "
                          "30-step FP32-inner regularised GMRES cycle without and one with deflation (r=20)")
+    ap.add_argument("--profile-fno", action="store_true",
+                    help="short fixed run for ncu captures of the tensor-core GEMMs: one forward and one backward "
+                         "pass of the 128^2 network on a batch of 4")
     ap.add_argument("--paper-table2", action="store_true",
                     help="the four systems of Table 2 on the three Section 4 squares (one JSON line)")
     ap.add_argument("--paper-table1", action="store_true",
@@ -315,6 +318,8 @@ def main():
         return reference_arm(args)
     if args.profile_driver:
         return profile_driver(args)
+    if args.profile_fno:
+        return profile_fno(args)
     if args.paper_table2:
         return paper_table2(args)
     if args.learned:
@@ -532,6 +537,21 @@ def profile_driver(args):
                      deflation=D)
     torch.cuda.synchronize()
     print(json.dumps({"profile_driver": "ok", "steps": [r1["iters"], r2["iters"]]}))
+    return 0
+
+
+def profile_fno(args):
+    """One forward and one backward pass of the default 128^2 network (batch 4)."""
+    import torch
+
+    from paper_1104_4263_gb300 import learned
+    net = learned.default_network(128, max_batch=4)
+    x = torch.randn(4, 6, 128, 128, device="cuda")
+    y = net.forward(x)
+    net.zero_grads()
+    net.backward(torch.randn_like(y))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_fno": "ok", "params": net.n_params}))
     return 0
 
 

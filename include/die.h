@@ -144,8 +144,8 @@ void dieop_destroy(dieop_t op);
  * Solves Atilde x = btilde with Atilde = A (regularized = 0) or A_R A and
  * btilde = A_R b (regularized = 1), right-preconditioned by the deflation
  * P^-1 of Eq. (4.12) when a defl_t is given: Atilde P^-1 v = btilde, x = P^-1 v.
- * Arnoldi by classical Gram-Schmidt with the DGKS criterion (by default a second pass
- * when the first removed more than half of ||w||^2), FP64; Hessenberg least squares by
+ * Arnoldi by classical Gram-Schmidt with the DGKS criterion (a second pass when the
+ * first left less than eta of ||w||; see reorth_eta), FP64; Hessenberg least squares by
  * Givens rotations, FP64, on the device.  With inner = DIE_FP32_INNER the products
  * with Atilde inside a cycle and the deflation P^-1 run in complex64 (a fixed
  * preconditioner for the whole solve); the restart residual stays FP64.
@@ -162,9 +162,10 @@ typedef struct gmres_opts {
                               FP64 restart residual (iterative refinement)                      */
     int timing;            /* 1: fill t_matvec/t_orth/t_defl (adds stream syncs)               */
     double reorth_eta;     /* DGKS threshold: second Gram-Schmidt pass when ||w'|| < eta ||w||;
-                              <= 0 selects 1/sqrt(2), the classical choice (the basis stays
-                              orthonormal to working precision at any restart); a smaller eta
-                              saves second passes but loses orthogonality as cycles grow;
+                              <= 0 selects 0.01 for restart <= 32 and the classical 1/sqrt(2)
+                              beyond (single-pass losses accumulate over a cycle: measured on
+                              the 512^2 core-shell, max |V*V - I| < 1e-8 after 30 steps at
+                              0.01, 3e-6 after 300 steps at 0.01, < 1e-8 at 1/sqrt(2));
                               >= 1 always re-orthogonalises                                    */
     int graph;             /* 1: the Arnoldi steps of a cycle run as one CUDA graph launch.  A
                               configuration (operator context, deflation handle, options, cycle

@@ -64,7 +64,7 @@ die_status fgmres_impl(dieop_s* op, fno_s* net, const gmres_opts* o, const doubl
     double2* h1 = w.small + 4;           // m + 3 slots each
     double2* h2 = h1 + (m + 3);
     double2* nrm = h2 + (m + 3);         // 2 slots
-    const double eta = o->reorth_eta > 0 ? o->reorth_eta : 0.7071067811865476;
+    const double eta = o->reorth_eta > 0 ? o->reorth_eta : default_reorth_eta(m);
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
 
     double bn2 = 0;
@@ -190,16 +190,25 @@ extern "C" die_status fgmres_solve(dieop_t op, fno_t net, defl_t defl, const gmr
         fo.use_x0 = nan ? 0 : 1;       // a NaN iterate is not a starting point
         fo.graph = 0;
         fo.timing = 0;
-        gmres_report r2{};
-        r2.history = nullptr;
-        s = gmres_solve(op, defl, &fo, b, x, &r2, stream);
-        if (s != DIE_OK && s != DIE_ENOCONV) return s;
-        r1.cycles += r2.cycles;
-        r1.iters += r2.iters;
-        r1.n_apply += r2.n_apply;
-        r1.rel_res_solved = r2.rel_res_orig;
-        r1.rel_res_orig = r2.rel_res_orig;
-        s = r2.rel_res_orig <= o->tol ? DIE_OK : DIE_ENOCONV;
+        // the regularised solve stops on its own residual ||A_R (b - A x)|| / ||A_R b||: tighten
+        // its tolerance (up to 1000x) until ||b - A x|| / ||b|| meets tol
+        int left = fallback_iters;
+        for (int tries = 0; tries < 4 && left > 0; tries++) {
+            gmres_report r2{};
+            fo.max_iters = left;
+            s = gmres_solve(op, defl, &fo, b, x, &r2, stream);
+            if (s != DIE_OK && s != DIE_ENOCONV) return s;
+            r1.cycles += r2.cycles;
+            r1.iters += r2.iters;
+            r1.n_apply += r2.n_apply;
+            r1.rel_res_solved = r2.rel_res_orig;
+            r1.rel_res_orig = r2.rel_res_orig;
+            left -= r2.iters;
+            if (r2.rel_res_orig <= o->tol || s == DIE_ENOCONV) break;
+            fo.tol *= 0.1;
+            fo.use_x0 = 1;
+        }
+        s = r1.rel_res_orig <= o->tol ? DIE_OK : DIE_ENOCONV;
     }
     if (rep) {
         double* hist = rep->history;

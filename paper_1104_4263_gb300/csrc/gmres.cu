@@ -3,8 +3,8 @@
 //
 // One cycle runs entirely on the device without host round trips.  Each Arnoldi
 // vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion: a second
-// pass only when the first left less than eta of ||w|| (eta = 1/sqrt(2), the classical
-// choice, unless the caller sets it).  Cycles start single-pass (the second-pass kernels are not launched); a
+// pass only when the first left less than eta of ||w|| (unless the caller sets eta: 0.01
+// for cycles of up to 32 steps, the classical 1/sqrt(2) for longer ones).  Cycles start single-pass (the second-pass kernels are not launched); a
 // cycle in which the criterion fires stops and runs again with the second passes, and
 // the solve keeps them.  The passes use the three-multiplication form of the complex
 // products (Re - Im of every basis vector is stored when the vector is normalised).
@@ -343,7 +343,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
                             gmres_report* rep, cudaStream_t ust, SolverCache* c, bool pin) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
-    const double eta = o->reorth_eta > 0 ? o->reorth_eta : kDefaultReorthEta;
+    const double eta = o->reorth_eta > 0 ? o->reorth_eta : default_reorth_eta(o->restart);
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
     const int m = o->restart;
     const long n = 2L * op->N;

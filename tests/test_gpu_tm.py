@@ -83,6 +83,6 @@ def test_tm_deflation():
     assert bool((D.apply(x)[1] == 0).all())
     b = op.plane_wave(0.4)
     xd = np.linalg.solve(A, b.cpu().numpy()[0].reshape(-1))
-    u, rep = op.solve(b, restart=10, tol=1e-10, max_iters=20000, deflation=D)
-    assert rep["converged"]
-    assert np.linalg.norm(u.cpu().numpy()[0].reshape(-1) - xd) / np.linalg.norm(xd) < 1e-8
+    u, rep = op.solve(b, restart=40, tol=1e-10, max_iters=20000, deflation=D)
+    assert rep["converged"], rep
+    assert np.linalg.norm(u.cpu().numpy()[0].reshape(-1) - xd) / np.linalg.norm(xd) < 1e-7
