@@ -498,6 +498,7 @@ def main():
     if not args.no_compare:
         _extra(out, "plain_fp64_same_budget", lambda: plain_fp64(op, b, args.step_iters, dt / args.steps, last))
         _extra(out, "time_to_tol", lambda: time_to_tol(die, W, torch))
+        _extra(out, "config2_to_tol", lambda: config2_to_tol(op, b, D, die, torch))
     if not args.no_cpu:
         try:
             out["cpu_baseline"] = cpu_oracle_rate(args.n)
@@ -708,6 +709,74 @@ def many_rates(die, W, torch, count: int = 16, n_angles: int = 4, iters: int = 2
             "note": "wall time around the host calls; gmres_solve_many runs up to 16 systems at once"}
 
 
+def config2_to_tol(op, b, D32, die, torch, k: int = 1000, budget: int = 2000):
+    """The metric's second half on the 512^2 core-shell: GMRES to 1e-6 under Section 5's
+    fair-memory rule with k = 1000 vectors -- plain FP64 GMRES(k) on A against GMRES(k - r)
+    on A_R A P^-1 (r = 20) with FP64 products and with FP32-inner products -- for a budget
+    of `budget` Arnoldi steps each.  On this object none reaches 1e-6 (the core's segment
+    [1, -2 + 0.1i] of Eq. (3.20) passes 0.033 from the origin, 0.017 after Eq. (5.3)): the
+    residual reached and the seconds per step are the comparison."""
+    marks = (100, 300, 1000, 2000)
+    out = {"fair_memory_vectors": k, "r": D32.r, "tol": TOL, "budget_steps": budget}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    D64 = die.Deflation(op, R_DEFL, tol=1e-4, regularized=True, inner=die.DIE_FP64)
+    torch.cuda.synchronize()
+    t_b64 = time.perf_counter() - t0
+    for name, kw in (("plain_fp64", dict(restart=k)),
+                     ("reg_defl_fp64", dict(restart=k - D64.r, regularized=True, deflation=D64)),
+                     ("reg_defl_mixed", dict(restart=k - D32.r, regularized=True, deflation=D32,
+                                             inner=die.DIE_FP32_INNER))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = op.solve(b, tol=TOL, max_iters=budget, history=budget, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h = rep["history"]
+        out[name] = {"restart": kw["restart"], "seconds": dt, "iters": rep["iters"], "converged": rep["converged"],
+                     "rel_res_solved": rep["rel_res_solved"], "rel_res_orig": rep["rel_res_orig"],
+                     "ms_per_step": 1e3 * dt / max(rep["iters"], 1), "n_reorth": rep["n_reorth"],
+                     "history": {m: float(h[m - 1]) for m in marks if m <= len(h)}}
+    out["deflation_build_s"] = {"fp64": t_b64}
+    out["note"] = ("residual estimates of the solved system at the marked steps; none of the three reaches 1e-6 "
+                   "(the same stagnation as the oracle's GMRES on the object at 64^2 and 128^2)")
+    out["core_shell_64"] = core_shell_small_to_tol(die, torch)
+    return out
+
+
+def core_shell_small_to_tol(die, torch, n: int = 64, k: int = 1500):
+    """The closest member of the core-shell family the method solves to 1e-6: the same
+    permittivities and cell size h = 1/64 on a 64^2 grid (a one-wavelength box), where
+    unrestarted GMRES converges (the oracle: about 700 steps on A_R A, 1500 on A).  Fair
+    memory k = 1500 vectors: plain FP64 GMRES(k) against A_R A P^-1 GMRES(k - r) in FP64 and
+    FP32-inner, r = 5 (the eigenvalues beyond the Section 5 radius at this size)."""
+    from paper_1104_4263_gb300 import workloads as W
+    p = W.config2(n)
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    rows = {}
+    for name, inner in (("plain_fp64", None), ("reg_defl_fp64", die.DIE_FP64), ("reg_defl_mixed", die.DIE_FP32_INNER)):
+        tb, D, kw = 0.0, None, dict(restart=k)
+        if inner is not None:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            D = die.Deflation(op, 5, tol=1e-4, regularized=True, inner=inner)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            kw = dict(restart=k - D.r, regularized=True, deflation=D, inner=inner)
+        op.solve(b, tol=TOL, max_iters=50, **kw)              # context and kernels warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = op.solve(b, tol=TOL, max_iters=6000, **kw)
+        torch.cuda.synchronize()
+        rows[name] = {"restart": kw["restart"], "seconds": time.perf_counter() - t0, "iters": rep["iters"],
+                      "converged": rep["converged"], "rel_res_orig": rep["rel_res_orig"], "deflation_build_s": tb}
+    base = rows["plain_fp64"]["seconds"]
+    for v in rows.values():
+        v["speedup_vs_plain_fp64"] = base / v["seconds"] if v["seconds"] > 0 else None
+    return {"grid": [n, n], "unknowns": 2 * p.N, "tol": TOL, **rows}
+
+
 def fp64_same_budget(op, b, step_iters, step_s, torch):
     """The headline configuration in its FP64 form: A_R A P^-1 with an FP64 deflation
     build (r = 20) and FP64 products inside the cycles, GMRES(30), the same step budget."""
@@ -903,8 +972,8 @@ PAPER_SWEEP_SIZE = {"r/2": (None, 2.4), "2r": (2.1, 5.1), "10r": (8.7, 46.6)}
 PAPER_SWEEP_EPS = {"2r": (1.8, 4.1), "10r": (1.6, 11.4)}
 
 
-def paper_sweeps(args, sizes=(1.0, 1.4, 1.8, 2.2), eps_values=(10.0, 14.0, 18.0), tol: float = 1e-8,
-                 max_iters: int = 400000):
+def paper_sweeps(args, sizes=(1.0, 1.6, 2.2), eps_values=(10.0, 15.0, 20.0), tol: float = 1e-8,
+                 max_iters: int = 60000):
     """Section 5's fair-memory experiments on lossless squares at 15 points per medium
     wavelength: for each object, r = the eigenvalues of A_R A outside the deflation radius
     (r = 0 in the deflation build), then for each memory rule restart(A_R A P^-1) = r/2, 2r,
@@ -945,7 +1014,7 @@ def paper_sweeps(args, sizes=(1.0, 1.4, 1.8, 2.2), eps_values=(10.0, 14.0, 18.0)
     return 0
 
 
-def paper_sinusoidal(args, tol: float = 1e-8, max_iters: int = 200000):
+def paper_sinusoidal(args, tol: float = 1e-8, max_iters: int = 60000):
     """Section 5's continuous-permittivity example (233 x 233, a = 4 wavelengths): A with
     restart 1620 against A_R A P^-1 with r = 180 and restart 1440, FP64, tol 1e-8; the
     paper's Matlab run took 162692 s and 11620 s (+ 775 s of eigs), a 14x (13.1x) speed-up."""
