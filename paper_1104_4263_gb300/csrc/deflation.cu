@@ -69,13 +69,14 @@ static die_status rotate_basis(const double2* Q, long n, int p, const double2* Z
     return DIE_OK;
 }
 
-// Device-side small eigenproblem of one Krylov-Schur restart (single thread, FP64).
+// Small eigenproblem of one Krylov-Schur restart, on the host (FP64; the same textbook
+// routines run on one GPU thread were 10x slower and made builds with Krylov dimensions
+// of a few hundred take minutes).
 //   B: (p+1) x p Rayleigh matrix (column-major, ld = p+1); row p holds beta e_{p-1}.
 //   Outputs: T (p x p Schur form, |T_ii| descending, ld = p), Z (p x p, ld = p),
-//   bvec (p): residual coefficients beta Z(p-1, :).  work: p entries; status[0] = 0 / -1.
-__global__ void ks_small_kernel(const double2* B, int p, double2* T, double2* Z, double2* bvec, double2* work,
-                                int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+//   bvec (p): residual coefficients beta Z(p-1, :).  Returns 0, or -1 if the QR iteration
+//   did not converge.
+static int ks_small_host(const double2* B, int p, double2* T, double2* Z, double2* bvec, std::vector<sd::cd>& work) {
     using sd::cd;
     cd* t = reinterpret_cast<cd*>(T);
     cd* z = reinterpret_cast<cd*>(Z);
@@ -85,7 +86,8 @@ __global__ void ks_small_kernel(const double2* B, int p, double2* T, double2* Z,
             t[(long)j * p + i] = cd{v.x, v.y};
             z[(long)j * p + i] = cd{i == j ? 1.0 : 0.0, 0.0};
         }
-    sd::hessenberg(t, p, z, p, p, reinterpret_cast<cd*>(work));
+    work.resize(p);
+    sd::hessenberg(t, p, z, p, p, work.data());
     const int rc = sd::schur_qr(t, p, z, p, p, 60);
     if (rc == 0) sd::schur_sort_desc(t, p, z, p, p);
     const double2 beta = B[(long)(p - 1) * (p + 1) + p];
@@ -93,7 +95,7 @@ __global__ void ks_small_kernel(const double2* B, int p, double2* T, double2* Z,
         const cd zz = z[(long)l * p + (p - 1)];
         bvec[l] = make_double2(beta.x * zz.re - beta.y * zz.im, beta.x * zz.im + beta.y * zz.re);
     }
-    status[0] = rc;
+    return rc;
 }
 
 // M = T^-1 - I for the r x r matrix T (column-major); status[0] = 0 / -1 (singular).
@@ -210,7 +212,9 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
     DIE_TRY(k_dots(w.Q, 0, 0, w.Q, n, 1, w.nrm, rs, nullptr, st));
     DIE_TRY(k_scale_inv_sqrt(w.Q, n, w.nrm, nullptr, st));
 
-    std::vector<double2> T(p * (size_t)p), bv(p);
+    std::vector<double2> T(p * (size_t)p), bv(p), Bh((size_t)(p + 1) * p), Zh(p * (size_t)p);
+    std::vector<sd::cd> swork;
+    double R_defl = -1.0;             // Section 5 deflation radius (r = 0), computed once
     int k = 0, nconv = 0;
     bool converged = false;
     for (int it = 0; it < max_restarts; it++) {
@@ -223,24 +227,27 @@ static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, d
             DIE_LAUNCH_CHECK();
             DIE_TRY(k_scale_inv_sqrt(wv, n, w.nrm + 1, nullptr, st));
         }
-        ks_small_kernel<<<1, 32, 0, st>>>(w.B, p, w.T, w.Z, w.bvec, w.work, w.ist);
-        DIE_LAUNCH_CHECK();
-        int rc = 0;
-        DIE_CUDA_TRY(cudaMemcpyAsync(T.data(), w.T, T.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        DIE_CUDA_TRY(cudaMemcpyAsync(bv.data(), w.bvec, bv.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        DIE_CUDA_TRY(cudaMemcpyAsync(&rc, w.ist, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DIE_CUDA_TRY(cudaMemcpyAsync(Bh.data(), w.B, Bh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
         DIE_CUDA_TRY(cudaStreamSynchronize(st));
+        const int rc = ks_small_host(Bh.data(), p, T.data(), Zh.data(), bv.data(), swork);
         if (rc != 0) return DIE_ENOCONV;
+        DIE_CUDA_TRY(cudaMemcpyAsync(w.T, T.data(), T.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DIE_CUDA_TRY(cudaMemcpyAsync(w.Z, Zh.data(), Zh.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DIE_CUDA_TRY(cudaMemcpyAsync(w.bvec, bv.data(), bv.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DIE_CUDA_TRY(cudaStreamSynchronize(st));     // the host buffers are refilled next restart
         if (auto_r) {
             // Section 5: deflate the eigenvalues outside the deflation radius (capped at r_max)
-            std::vector<double> eps(2 * (size_t)op->N);
-            DIE_CUDA_TRY(cudaMemcpy(eps.data(), op->chi_d, op->N * sizeof(double2), cudaMemcpyDeviceToHost));
-            for (long i = 0; i < op->N; i++) eps[2 * i] += 1.0;                 // eps_r = chi + 1
-            double R = die_deflation_radius(eps.data(), op->N, 1000);
-            if (!reg) {
-                R = 0;                                                         // unregularised: |eps_r| max
-                for (long i = 0; i < op->N; i++) R = fmax(R, hypot(eps[2 * i], eps[2 * i + 1]));
+            if (R_defl < 0) {
+                std::vector<double> eps(2 * (size_t)op->N);
+                DIE_CUDA_TRY(cudaMemcpy(eps.data(), op->chi_d, op->N * sizeof(double2), cudaMemcpyDeviceToHost));
+                for (long i = 0; i < op->N; i++) eps[2 * i] += 1.0;                 // eps_r = chi + 1
+                R_defl = die_deflation_radius(eps.data(), op->N, 1000);
+                if (!reg) {
+                    R_defl = 0;                                                    // unregularised: |eps_r| max
+                    for (long i = 0; i < op->N; i++) R_defl = fmax(R_defl, hypot(eps[2 * i], eps[2 * i + 1]));
+                }
             }
+            const double R = R_defl;
             int cnt = 0;
             while (cnt < rmax && cnt < p - 1 && hypot(T[(size_t)cnt * p + cnt].x, T[(size_t)cnt * p + cnt].y) > R) cnt++;
             if (cnt < 1) cnt = 1;

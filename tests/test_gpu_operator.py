@@ -256,3 +256,31 @@ def test_edge_and_hot_cell_inputs_fast_path(n):
         assert rel(op.apply_regularized(dev(x)).cpu().numpy(), yr) < FP64_TOL, name
         assert rel(op32.apply(dev(x, torch.complex64)).cpu().numpy(), ya) < C64_TOL, name
         assert rel(op32.apply_regularized(dev(x, torch.complex64)).cpu().numpy(), yr) < C64_TOL, name
+
+
+def test_set_permittivity_equals_fresh_operator():
+    """dieop_set_permittivity: the products of an operator given a new map equal those of an
+    operator created with it (bit for bit: same Green spectra, same contrasts); a deflation
+    handle of the old map is rejected; a map violating the existence condition is refused
+    and leaves the previous one in place."""
+    rng = W.rng_for(140)
+    e1 = W.random_field(rng, 40, 33, 1.0, 9.0)
+    e2 = W.random_field(rng, 40, 33, -4.0, 16.0)
+    h = 0.03
+    op = die.Operator(e1, h)
+    D = die.Deflation(op, 4, tol=1e-4, regularized=True)
+    x = dev(W.random_vector(rng, 40, 33))
+    op.set_permittivity(e2)
+    fresh = die.Operator(e2, h)
+    assert torch.equal(op.apply(x), fresh.apply(x))
+    assert torch.equal(op.apply_regularized(x), fresh.apply_regularized(x))
+    with pytest.raises(die.DieError):
+        op.solve(op.plane_wave(0.0), regularized=True, deflation=D, max_iters=5)
+    bad = e2.copy()
+    bad[3, 4] = 0.0
+    with pytest.raises(die.DieError) as e:
+        op.set_permittivity(bad)
+    assert e.value.code == 4
+    assert torch.equal(op.apply(x), fresh.apply(x))
+    op.set_permittivity(torch.from_numpy(e1).cuda())
+    assert torch.equal(op.apply(x), die.Operator(e1, h).apply(x))
