@@ -53,13 +53,13 @@ WORKLOAD = ("core-shell 512x512 (eps -2+0.1i core R1.5, 20+0.5i shell R2.5, side
             "FP32 products + FP64 Krylov, 1500 Arnoldi steps per step")
 L2_NOTE = "working set > L2 (Krylov basis 31 x 8.4 MB, deflation basis 20 x 4.2 MB)"
 # ncu DRAM bytes (read + write) of one launch of the FP64 projection kernel on this
-# workload: 16 basis vectors with their Re - Im planes, and the norm of w, over
+# workload: 13 basis vectors with their Re - Im planes, and the norm of w, over
 # 2N = 524288, from one capture of the committed profile driver (bench.py
 # --profile-driver; the kernel is unchanged since).  Its traffic grows with the vectors
 # read, so it is scaled to the bench's average launch by the algorithmic bytes.
-NCU_DOTS = {"dram_bytes": 213.669888e6 + 3.034880e6, "nv": 16, "n": 524288,
-            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:proj3 on "
-                      "bench.py --profile-driver (one 16-vector launch)"}
+NCU_DOTS = {"dram_bytes": 175.310848e6 + 0.329984e6, "nv": 13, "n": 524288,
+            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:proj3 -s 10 -c 3 on "
+                      "bench.py --profile-driver (the 13-vector launch)"}
 
 
 def fp64_peak(die):

@@ -552,11 +552,14 @@ die_status create_impl(const fno_desc* d, fno_s* f) {
     return make_dft(f);
 }
 
+// Reads (and clears) the flag a GEMM sets when one of its bounded waits gave up.
 die_status check_err(fno_s* f, cudaStream_t st) {
     int e = 0;
     DIE_CUDA_TRY(cudaMemcpyAsync(&e, f->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     DIE_CUDA_TRY(cudaStreamSynchronize(st));
-    return e ? DIE_ETIMEOUT : DIE_OK;
+    if (!e) return DIE_OK;
+    DIE_CUDA_TRY(cudaMemsetAsync(f->err, 0, sizeof(int), st));
+    return DIE_ETIMEOUT;
 }
 
 }  // namespace

@@ -197,20 +197,14 @@ die_status tc_gemm(const GemmArgs& g, cudaStream_t st) {
     if (!g.A || !g.B || !g.C) return DIE_EINVAL;
     const size_t smem = 2 * kRegion + 16;
     const dim3 block(kThreads);
+    // the shared-memory limit is raised on every call (a host-side attribute, cheap, and
+    // correct on whichever device is current)
     if (g.N <= 64) {
-        static bool attr = false;        // raised once per process (same value every time)
-        if (!attr) {
-            DIE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
+        DIE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const dim3 grid((g.M + kBM - 1) / kBM, (g.N + 63) / 64, g.batch);
         tc_gemm_kernel<64><<<grid, block, smem, st>>>(g);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            DIE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
+        DIE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const dim3 grid((g.M + kBM - 1) / kBM, (g.N + 127) / 128, g.batch);
         tc_gemm_kernel<128><<<grid, block, smem, st>>>(g);
     }

@@ -152,10 +152,11 @@ def test_fgmres_with_untrained_network_converges():
     x, rep = die.fgmres(op, b, net=net, restart=20, tol=1e-8, max_iters=3000)
     assert rep["converged"] and not rep["used_fallback"]
     assert _rel(x.cpu().numpy().reshape(-1), xd) < 1e-5
-    # the fallback: regularised FP32-inner GMRES(20) (no deflation: this rotationally symmetric
-    # object has degenerate eigenvalue pairs that a small rank can split)
+    # the fallback: regularised FP32-inner GMRES(60) (no deflation: this rotationally symmetric
+    # object has degenerate eigenvalue pairs that a small rank can split; GMRES(20) on the
+    # regularised system stagnates for this incidence angle)
     x2, rep2 = die.fgmres(op, b, net=net, restart=10, tol=1e-6, max_iters=5,
-                          fallback_restart=20, fallback_iters=5000)
+                          fallback_restart=60, fallback_iters=5000)
     assert rep2["used_fallback"] and rep2["converged"] and rep2["rel_res_orig"] <= 1e-6, rep2
     assert _rel(x2.cpu().numpy().reshape(-1), xd) < 1e-3
 
