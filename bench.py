@@ -495,6 +495,7 @@ def main():
     _extra(out, "batch_solve", lambda: [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)])
     _extra(out, "small_grids", lambda: small_grid_rates(die, W, torch))
     _extra(out, "many_systems", lambda: many_rates(die, W, torch))
+    _extra(out, "config3", lambda: config3_rates(die, W, torch))
     if not args.no_compare:
         _extra(out, "plain_fp64_same_budget", lambda: plain_fp64(op, b, args.step_iters, dt / args.steps, last))
         _extra(out, "time_to_tol", lambda: time_to_tol(die, W, torch))
@@ -795,6 +796,43 @@ def fp64_same_budget(op, b, step_iters, step_s, torch):
             "rel_res_solved": rep["rel_res_solved"], "rel_res_orig": rep["rel_res_orig"],
             "deflation_build_s": tb, "seconds_ratio_vs_step": dt / step_s,
             "note": "FP64 products and FP64 deflation inside the cycles; same budget as the timed (FP32-inner) step"}
+
+
+def config3_rates(die, W, torch, tol: float = 1e-6, max_iters: int = 3000):
+    """The batched workload: 64 Gaussian-field scatterers on grids drawn from {64, ..., 512},
+    8 incidence angles each (512 right-hand sides), complex64 products with FP64 refinement
+    (regularised, FP32-inner GMRES(30)), every system to `tol` (at most `max_iters` steps).
+    Right-hand sides solved per second one after another (gmres_solve) and all together
+    (gmres_solve_many, cycles as CUDA graphs); the two runs' Arnoldi step counts are
+    compared system by system."""
+    probs = W.config3(64)
+    ops, bs = [], []
+    for q in probs:
+        op = die.Operator(q.eps_r, q.h)
+        for psi in q.psi:
+            ops.append(op)
+            bs.append(op.plane_wave(psi))
+    kw = dict(restart=RESTART, tol=tol, max_iters=max_iters, regularized=True, inner=die.DIE_FP32_INNER)
+    for k in range(0, len(ops), 8):                       # contexts allocated, kernels warm
+        ops[k].solve(bs[k].clone(), **dict(kw, max_iters=30))
+    die.solve_many(ops[:16], bs[:16], graph=True, **dict(kw, max_iters=30))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [op.solve(b.clone(), **kw)[1] for op, b in zip(ops, bs)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, reps = die.solve_many(ops, bs, graph=True, **kw)
+    torch.cuda.synchronize()
+    t_many = time.perf_counter() - t0
+    same = sum(a["iters"] == r["iters"] for a, r in zip(seq, reps))
+    sizes = sorted({q.n1 for q in probs})
+    return {"scatterers": len(probs), "right_hand_sides": len(ops), "grid_sizes": sizes, "tol": tol,
+            "converged": sum(r["converged"] for r in reps), "arnoldi_steps": sum(r["iters"] for r in reps),
+            "sequential_rhs_per_s": len(ops) / t_seq, "many_graph_rhs_per_s": len(ops) / t_many,
+            "speedup": t_seq / t_many, "sequential_s": t_seq, "many_s": t_many,
+            "same_step_counts": same,
+            "note": "gmres_solve_many runs up to 16 systems at once; wall time around the host calls"}
 
 
 def plain_fp64(op, b, step_iters, step_s, last):

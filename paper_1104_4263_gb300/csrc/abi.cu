@@ -72,15 +72,39 @@ int choose_fft_size(int n) {
     return best;
 }
 
+// Twiddle arrays of 3 L entries: [0, L) the natural table exp(-2 pi i m / L); for
+// L = 2^a in [256, 4096] (the compile-time stages of fft_fast.cuh), [L, 2 L) and
+// [2 L, 3 L) the stage tables of the forward and inverse plans: stage s (radix R,
+// sub-transform length Ns) keeps at r Ns + k - 1 (1 <= r < R, k < Ns) the natural entry
+// of index (L / (Ns R)) r k, i.e. exp(-2 pi i r k / (Ns R)).  Stage s covers
+// [Ns - 1, Ns R - 1), so the stages tile [0, L - 1); the entries a thread reads in one
+// stage are consecutive in k instead of L / (Ns R) r apart.
+template <typename V>
+static void stage_table(int L, bool inv, const V* nat, V* out) {
+    const FftPlan p = pow2_plan(L, inv);
+    out[L - 1] = nat[0];
+    for (int s = 0, ns = 1; s < p.ns; ns *= p.radix[s], s++) {
+        const int R = p.radix[s], step = L / (ns * R);
+        for (int r = 1; r < R; r++)
+            for (int k = 0; k < ns; k++) out[r * ns + k - 1] = nat[(long)step * r * k];
+    }
+}
+
 static void twiddles(int L, std::vector<double2>& d, std::vector<float2>& f) {
-    d.resize(L);
-    f.resize(L);
+    d.assign(3 * (size_t)L, make_double2(0.0, 0.0));
+    f.assign(3 * (size_t)L, make_float2(0.f, 0.f));
     const long double two_pi = 6.283185307179586476925286766559005768L;
     for (int m = 0; m < L; m++) {
         const long double ang = two_pi * (long double)m / (long double)L;
         const double c = (double)cosl(ang), s = -(double)sinl(ang);
         d[m] = make_double2(c, s);
         f[m] = make_float2((float)c, (float)s);
+    }
+    if (L >= 256 && L <= 4096 && (L & (L - 1)) == 0) {
+        for (int inv = 0; inv < 2; inv++) {
+            stage_table(L, inv != 0, d.data(), d.data() + (1 + inv) * (size_t)L);
+            stage_table(L, inv != 0, f.data(), f.data() + (1 + inv) * (size_t)L);
+        }
     }
 }
 
@@ -155,10 +179,10 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     op->Q2 = op->M2 / 2 + 1;
     DIE_CUDA_TRY(cudaGetDevice(&op->device));
     const long N = op->N, q = (long)op->Q1 * op->Q2;
-    DIE_TRY(dmalloc(&op->tw1_d, op->M1 * sizeof(double2)));
-    DIE_TRY(dmalloc(&op->tw2_d, op->M2 * sizeof(double2)));
-    DIE_TRY(dmalloc(&op->tw1_f, op->M1 * sizeof(float2)));
-    DIE_TRY(dmalloc(&op->tw2_f, op->M2 * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->tw1_d, 3 * (size_t)op->M1 * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->tw2_d, 3 * (size_t)op->M2 * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->tw1_f, 3 * (size_t)op->M1 * sizeof(float2)));
+    DIE_TRY(dmalloc(&op->tw2_f, 3 * (size_t)op->M2 * sizeof(float2)));
     DIE_TRY(dmalloc(&op->gq_d, 3 * q * sizeof(double2)));
     DIE_TRY(dmalloc(&op->gq_f, 3 * q * sizeof(float2)));
     DIE_TRY(dmalloc(&op->chi_d, N * sizeof(double2)));
@@ -177,10 +201,10 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     std::vector<float2> t1f, t2f;
     twiddles(op->M1, t1d, t1f);
     twiddles(op->M2, t2d, t2f);
-    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_d, t1d.data(), op->M1 * sizeof(double2), cudaMemcpyHostToDevice, st));
-    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_d, t2d.data(), op->M2 * sizeof(double2), cudaMemcpyHostToDevice, st));
-    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_f, t1f.data(), op->M1 * sizeof(float2), cudaMemcpyHostToDevice, st));
-    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_f, t2f.data(), op->M2 * sizeof(float2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_d, t1d.data(), t1d.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_d, t2d.data(), t2d.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw1_f, t1f.data(), t1f.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_f, t2f.data(), t2f.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
 
     double2* scratch = nullptr;
     const size_t scratch_bytes = 3 * (size_t)op->M1 * op->M2 * sizeof(double2) + (eps_on_device ? 0 : N * sizeof(double2));

@@ -14,6 +14,11 @@
 //  * While Ns divides G (every stage but possibly the last), the twiddle index
 //    k = (t + b G) mod Ns is the same for all butterflies of a thread, so the R - 1
 //    twiddles are loaded once per stage.
+//  * Twiddles come from per-stage tables (the `twx` arrays of the operator): the factor
+//    exp(-2 pi i r k / (Ns R)) of a stage sits at r Ns + k - 1 of its plan's table
+//    (forward plan at [0, L), inverse plan at [L, 2 L)), so the threads of a warp read
+//    consecutive entries.  In the natural table the same factors are L r / (Ns R)
+//    entries apart and one warp's load touches up to 16 cache lines.
 #pragma once
 
 #include "fft.cuh"
@@ -52,6 +57,7 @@ struct FStage {
     static constexpr int kR = R;
     static constexpr int G = L / 16, B = 16 / R, LR = L / R;
     static constexpr bool kUniformK = (G % NS) == 0;    // twiddle index shared by the thread's butterflies
+    static constexpr int kTwBase = INV ? L : 0;          // this plan's part of the stage tables
     static_assert(kUniformK || B * G <= NS, "last-stage layout");
     static_assert(padding_linear<L, R, NS>(), "shared-memory padding is not linear over this stage's accesses");
 
@@ -70,13 +76,13 @@ struct FStage {
     // twiddles, then the radix-R DFTs
     __host__ __device__ static __forceinline__ void compute(V (&x)[16], int t, const V* __restrict__ tw) {
         if constexpr (NS > 1) {
-            constexpr int step = L / (NS * R);     // tw[step * r * k] = exp(-2 pi i r k / (NS R))
+            // tw[kTwBase + r NS + k - 1] = exp(-2 pi i r k / (NS R))
             if constexpr (kUniformK) {
                 const int k = t & (NS - 1);
                 V w[R];
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    w[r] = ld_tw(&tw[step * r * k]);
+                    w[r] = ld_tw(&tw[kTwBase + r * NS + k - 1]);
                     if (INV) w[r].y = -w[r].y;
                 }
 #pragma unroll
@@ -89,7 +95,7 @@ struct FStage {
                     const int k = t + b * G;
 #pragma unroll
                     for (int r = 1; r < R; r++) {
-                        V w = ld_tw(&tw[step * r * k]);
+                        V w = ld_tw(&tw[kTwBase + r * NS + k - 1]);
                         if (INV) w.y = -w.y;
                         x[b * R + r] = cmul(x[b * R + r], w);
                     }
@@ -117,12 +123,11 @@ struct FStage {
     // twiddles loaded once for both.
     __host__ __device__ static __forceinline__ void compute2(V (&x0)[16], V (&x1)[16], int t, const V* __restrict__ tw) {
         if constexpr (NS > 1) {
-            constexpr int step = L / (NS * R);
             if constexpr (kUniformK) {
                 const int k = t & (NS - 1);
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    V w = ld_tw(&tw[step * r * k]);
+                    V w = ld_tw(&tw[kTwBase + r * NS + k - 1]);
                     if (INV) w.y = -w.y;
 #pragma unroll
                     for (int b = 0; b < B; b++) {
@@ -136,7 +141,7 @@ struct FStage {
                     const int k = t + b * G;
 #pragma unroll
                     for (int r = 1; r < R; r++) {
-                        V w = ld_tw(&tw[step * r * k]);
+                        V w = ld_tw(&tw[kTwBase + r * NS + k - 1]);
                         if (INV) w.y = -w.y;
                         x0[b * R + r] = cmul(x0[b * R + r], w);
                         x1[b * R + r] = cmul(x1[b * R + r], w);

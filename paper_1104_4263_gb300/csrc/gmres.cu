@@ -4,7 +4,8 @@
 // One cycle runs entirely on the device without host round trips.  Each Arnoldi
 // vector is orthogonalised by classical Gram-Schmidt with the DGKS criterion: a second
 // pass only when the first left less than eta of ||w|| (unless the caller sets eta: 0.01
-// for cycles of up to 32 steps, the classical 1/sqrt(2) for longer ones).  Cycles start single-pass (the second-pass kernels are not launched); a
+// for cycles of up to 64 steps, the classical 1/sqrt(2) for longer ones).  Cycles start
+// single-pass (the second-pass kernels are not launched); a
 // cycle in which the criterion fires stops and runs again with the second passes, and
 // the solve keeps them.  The passes use the three-multiplication form of the complex
 // products (Re - Im of every basis vector is stored when the vector is normalised).

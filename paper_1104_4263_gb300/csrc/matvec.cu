@@ -8,6 +8,7 @@ OpDev<double> view_d(const dieop_s* op) {
     v.n1 = op->n1; v.n2 = op->n2; v.M1 = op->M1; v.M2 = op->M2; v.Q1 = op->Q1; v.Q2 = op->Q2;
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_d; v.tw2 = op->tw2_d; v.gq = op->gq_d;
+    v.twx1 = op->tw1_d + op->M1; v.twx2 = op->tw2_d + op->M2;
     v.xs = 2L * op->n1 * op->n2;
     v.ws = 2L * op->M1 * op->n2;
     return v;
@@ -17,6 +18,7 @@ OpDev<float> view_f(const dieop_s* op) {
     v.n1 = op->n1; v.n2 = op->n2; v.M1 = op->M1; v.M2 = op->M2; v.Q1 = op->Q1; v.Q2 = op->Q2;
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_f; v.tw2 = op->tw2_f; v.gq = op->gq_f;
+    v.twx1 = op->tw1_f + op->M1; v.twx2 = op->tw2_f + op->M2;
     v.xs = 2L * op->n1 * op->n2;
     v.ws = 2L * op->M1 * op->n2;
     return v;

@@ -392,11 +392,11 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
             const int idx = F0::index(e);
             x[e] = idx < n1 ? cmul(cvt<C>(ur[idx]), cr[idx]) : czero<C>();
         }
-        F0::compute(x, t, op.tw1);
+        F0::compute(x, t, op.twx1);
         F0::store(buf, x, t);
     }
     __syncthreads();
-    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.tw1, active);
+    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.twx1, active);
     tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
 }
 
@@ -481,11 +481,11 @@ __global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, c
                 x[e] = czero<C>();
             }
         }
-        F0::compute(x, t, op.tw1);
+        F0::compute(x, t, op.twx1);
         F0::store(buf, x, t);
     }
     __syncthreads();
-    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.tw1, active);
+    run_fast<C, L, false, 1, P2<L>::fwd.ns, false>(buf, x, t, op.twx1, active);
     tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
 }
 
@@ -531,10 +531,10 @@ __global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_f
         const int idx = F0::index(e);
         x[e] = idx < n2 ? col[idx] : czero<C>();
     }
-    F0::compute(x, t, op.tw2);
+    F0::compute(x, t, op.twx2);
     F0::store(buf, x, t);
     __syncthreads();
-    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.tw2, true);
+    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.twx2, true);
     if (stage_g) {
         cp_async_wait_all();
         __syncthreads();
@@ -561,12 +561,12 @@ __global__ void __launch_bounds__(2 * (L / 16), k2_min_blocks<C_t<T>, L>()) k2_f
         }
     }
     __syncthreads();
-    I0::compute(x, t, op.tw2);
+    I0::compute(x, t, op.twx2);
     I0::store(buf, x, t);
     __syncthreads();
-    run_fast<C, L, true, 1, nsi - 1, false>(buf, x, t, op.tw2, true);
+    run_fast<C, L, true, 1, nsi - 1, false>(buf, x, t, op.twx2, true);
     IL::load(buf, x, t);
-    IL::compute(x, t, op.tw2);
+    IL::compute(x, t, op.twx2);
 #pragma unroll
     for (int e = 0; e < 16; e++) {
         const int idx = IL::index(e);
@@ -623,14 +623,14 @@ __global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T>
         x0[e] = idx < n2 ? col0[idx] : czero<C>();
         x1[e] = idx < n2 ? col1[idx] : czero<C>();
     }
-    F0::compute2(x0, x1, t, op.tw2);
+    F0::compute2(x0, x1, t, op.twx2);
     F0::store(buf0, x0, t);
     F0::store(buf1, x1, t);
     __syncthreads();
-    run_fast2<C, L, false, 1, nsf - 1>(buf0, buf1, x0, x1, t, op.tw2);
+    run_fast2<C, L, false, 1, nsf - 1>(buf0, buf1, x0, x1, t, op.twx2);
     FL::load(buf0, x0, t);
     FL::load(buf1, x1, t);
-    FL::compute2(x0, x1, t, op.tw2);
+    FL::compute2(x0, x1, t, op.twx2);
     if (stage_g) cp_async_wait_all();
     __syncthreads();             // spectra visible; every thread has read its last forward stage
     {   // 2 x 2 Green-spectrum multiply at k2 = t + c (c = I0::index(e))
@@ -655,14 +655,14 @@ __global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T>
             x1[e] = cadd(cmul(go, u0), cmul(b, u1));
         }
     }
-    I0::compute2(x0, x1, t, op.tw2);
+    I0::compute2(x0, x1, t, op.twx2);
     I0::store(buf0, x0, t);
     I0::store(buf1, x1, t);
     __syncthreads();
-    run_fast2<C, L, true, 1, nsi - 1>(buf0, buf1, x0, x1, t, op.tw2);
+    run_fast2<C, L, true, 1, nsi - 1>(buf0, buf1, x0, x1, t, op.twx2);
     IL::load(buf0, x0, t);
     IL::load(buf1, x1, t);
-    IL::compute2(x0, x1, t, op.tw2);
+    IL::compute2(x0, x1, t, op.twx2);
 #pragma unroll
     for (int e = 0; e < 16; e++) {
         const int idx = IL::index(e);
@@ -695,10 +695,10 @@ __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __rest
     tile_io<C, L, TR, false>(tile, const_cast<C*>(W), c, i2_0, op.n2);
     __syncthreads();
     C x[16];
-    run_fast<C, L, true, 0, ns - 1, false>(buf, x, t, op.tw1, active);
+    run_fast<C, L, true, 0, ns - 1, false>(buf, x, t, op.twx1, active);
     if (!active) return;
     IL::load(buf, x, t);
-    IL::compute(x, t, op.tw1);
+    IL::compute(x, t, op.twx1);
 #pragma unroll
     for (int e = 0, q = 0; e < 16; e++) {
         const int idx = IL::index(e);
@@ -736,10 +736,10 @@ __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict
     tile_io<C, L, TR, false>(tile, W, c, i2_0, op.n2);
     __syncthreads();
     C x[16];
-    run_fast<C, L, true, 0, nsi - 1, false>(buf, x, t, op.tw1, active);
+    run_fast<C, L, true, 0, nsi - 1, false>(buf, x, t, op.twx1, active);
     if (active) {
         IL::load(buf, x, t);
-        IL::compute(x, t, op.tw1);
+        IL::compute(x, t, op.twx1);
         // v = u - z (first product), kept for the final subtraction; then chi' v -> FFT
 #pragma unroll
         for (int e = 0, q = 0; e < 16; e++) {
@@ -756,11 +756,11 @@ __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict
     }
     __syncthreads();            // every thread has read its last inverse stage from the tile
     if (active) {
-        F0::compute(x, t, op.tw1);
+        F0::compute(x, t, op.twx1);
         F0::store(buf, x, t);
     }
     __syncthreads();
-    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.tw1, active);
+    run_fast<C, L, false, 1, nsf, false>(buf, x, t, op.twx1, active);
     tile_io<C, L, TR, true>(tile, W, c, i2_0, op.n2);
 }
 

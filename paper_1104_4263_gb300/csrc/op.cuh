@@ -14,6 +14,8 @@ struct OpDev {
     FftPlan f1, i1, f2, i2;       // forward / inverse plans along x1 (length M1) and x2 (M2)
     const C* tw1;                 // exp(-2 pi i m / M1), m < M1
     const C* tw2;                 // exp(-2 pi i m / M2)
+    const C* twx1;                // stage tables of the compile-time plans along x1 (2 M1)
+    const C* twx2;                // the same along x2 (2 M2)
     const C* gq;                  // quarter spectra of G11, G22, G12: [plane][k1q][k2q], pre-scaled
     long xs;                      // batched products: elements per field vector (2 n1 n2)
     long ws;                      // batched products: elements per set of row spectra (2 M1 n2)
@@ -34,8 +36,8 @@ struct dieop_s {
     die_precision prec = DIE_FP64;
     die_polarization pol = DIE_TE;
     die::FftPlan f1{}, i1{}, f2{}, i2{};
-    double2 *tw1_d = nullptr, *tw2_d = nullptr;
-    float2 *tw1_f = nullptr, *tw2_f = nullptr;
+    double2 *tw1_d = nullptr, *tw2_d = nullptr;   // 3 M entries: natural table, then the
+    float2 *tw1_f = nullptr, *tw2_f = nullptr;    // forward and inverse stage tables
     double2* gq_d = nullptr;       // 3 * Q1 * Q2
     float2* gq_f = nullptr;
     double2 *chi_d = nullptr, *chir_d = nullptr;   // chi = eps_r - 1, chi' = 1/eps_r - 1

@@ -1,4 +1,5 @@
 // Kernel timing aid (see prof.cuh) and its C ABI.
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -6,7 +7,7 @@
 
 namespace die {
 
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 thread_local int g_prof_override = -1;
 
 namespace {
@@ -17,8 +18,10 @@ struct Rec {
 std::vector<cudaEvent_t> g_pool;         // reusable events
 size_t g_used = 0;
 std::vector<Rec> g_recs;
-int g_open_id = -1;
-cudaEvent_t g_open_ev = nullptr;
+std::mutex g_mu;                         // the pool and the records: host threads of the
+                                         // concurrent solvers launch at the same time
+thread_local int g_open_id = -1;         // the launch bracketed by this thread
+thread_local cudaEvent_t g_open_ev = nullptr;
 long long g_launches[PK_COUNT];
 double g_ms[PK_COUNT];
 bool g_overflow = false;
@@ -44,6 +47,7 @@ const char* kNames[PK_COUNT] = {"rows_fwd", "cols_green", "rows_inv", "rows_inv_
 }  // namespace
 
 void prof_mark(int id, cudaStream_t st, int stop) {
+    std::lock_guard<std::mutex> lock(g_mu);
     if (!stop) {
         g_open_ev = next_event();
         g_open_id = id;
@@ -70,6 +74,7 @@ using namespace die;
 extern "C" {
 
 die_status die_prof_begin(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
     for (int i = 0; i < PK_COUNT; i++) { g_launches[i] = 0; g_ms[i] = 0; }
     g_recs.clear();
     g_used = 0;
@@ -81,6 +86,7 @@ die_status die_prof_begin(void) {
 die_status die_prof_end(void) {
     g_prof_on = false;
     DIE_CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lock(g_mu);
     for (const Rec& r : g_recs) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {

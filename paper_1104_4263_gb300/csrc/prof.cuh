@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace die {
 
 enum ProfKernel {
@@ -26,7 +28,7 @@ enum ProfKernel {
     PK_COUNT
 };
 
-extern bool g_prof_on;
+extern std::atomic<bool> g_prof_on;
 extern thread_local int g_prof_override;      // >= 0: record launches under this class instead
 void prof_mark(int id, cudaStream_t st, int stop);
 

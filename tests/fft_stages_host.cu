@@ -38,10 +38,18 @@ double max_rel_err() {
     using F0 = typename PlanStage<V, L, INV, 0>::St;
     using FL = typename PlanStage<V, L, INV, pl.ns - 1>::St;
     const long double pi = 3.141592653589793238462643383279502884L;
-    std::vector<V> tw(L), buf(padded_len(L));
-    for (int m = 0; m < L; m++) {
-        const long double a = -2.0L * pi * m / L;
-        tw[m] = mk((T)std::cos(a), (T)std::sin(a));
+    // stage tables as the fast stages read them: the forward plan at [0, L), the inverse
+    // plan at [L, 2 L); stage (radix R, sub-transform length Ns) holds
+    // exp(-2 pi i r k / (Ns R)) at r Ns + k - 1 for 1 <= r < R, k < Ns
+    std::vector<V> tw(2 * L), buf(padded_len(L));
+    for (int part = 0; part < 2; part++) {
+        const FftPlan p = part ? P2<L>::inv : P2<L>::fwd;
+        for (int st = 0, ns = 1; st < p.ns; ns *= p.radix[st], st++)
+            for (int r = 1; r < p.radix[st]; r++)
+                for (int k = 0; k < ns; k++) {
+                    const long double a = -2.0L * pi * (long double)(r * k) / (long double)(ns * p.radix[st]);
+                    tw[part * L + r * ns + k - 1] = mk((T)std::cos(a), (T)std::sin(a));
+                }
     }
     std::vector<std::complex<long double>> in(L);
     unsigned s = 20110421u;                       // fixed LCG: the input needs no other source

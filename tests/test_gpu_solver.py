@@ -321,11 +321,12 @@ def _orthogonality(op, first, count):
 
 
 @pytest.mark.parametrize("restart,inner,defl_r", [(30, die.DIE_FP32_INNER, 20), (30, die.DIE_FP64, 0),
-                                                  (300, die.DIE_FP32_INNER, 20)])
+                                                  (64, die.DIE_FP32_INNER, 20), (300, die.DIE_FP32_INNER, 20)])
 def test_basis_orthogonality_512(restart, inner, defl_r):
-    """One full cycle on the 512^2 core-shell at the default re-orthogonalisation threshold:
-    the Arnoldi vectors v_1 .. v_{m-1} the cycle leaves are orthonormal to 1e-8 (max entry of
-    V* V - I), also across the chunk boundary of a 300-vector basis."""
+    """One full cycle on the 512^2 core-shell at the default re-orthogonalisation threshold
+    (0.01 up to 64 steps, 1/sqrt(2) beyond): the Arnoldi vectors v_1 .. v_{m-1} the cycle
+    leaves are orthonormal to 1e-8 (max entry of V* V - I), also across the chunk boundary
+    of a 300-vector basis."""
     p = W.config2(512)
     op = die.Operator(p.eps_r, p.h)
     b = op.plane_wave(0.0)
