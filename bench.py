@@ -290,6 +290,8 @@ def main():
     ap.add_argument("--step-iters", type=int, default=STEP_ITERS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 and time-to-tol comparisons")
+    ap.add_argument("--single-system", action="store_true",
+                    help="skip the sections that solve several systems at once (host threads)")
     ap.add_argument("--profile-driver", action="store_true",
                     help="short fixed run for ncu captures: one complex64 regularised product, then one "
                          "30-step FP32-inner regularised GMRES cycle without and one with deflation (r=20)")
@@ -306,6 +308,13 @@ def main():
     ap.add_argument("--paper-sinusoidal", action="store_true",
                     help="Section 5's sinusoidal 4-wavelength object: A with restart 1620 against A_R A P^-1 with "
                          "r = 180 and restart 1440 (one JSON line)")
+    ap.add_argument("--config3", action="store_true",
+                    help="the batched workload: 64 random scatterers x 8 angles (512 right-hand sides) to 1e-6, "
+                         "one after another and concurrently with graph cycles (one JSON line)")
+    ap.add_argument("--config5", action="store_true",
+                    help="the 2048^2 composite of 400 random cylinders: plain FP64 GMRES(40) and GMRES(80) against "
+                         "A_R A P^-1 (r = 40) GMRES(40) in FP64 and FP32-inner, a fixed step budget (one JSON line)")
+    ap.add_argument("--budget", type=int, default=1000, help="--config5: Arnoldi steps per solve")
     ap.add_argument("--learned", action="store_true",
                     help="learned preconditioner: solver-generated pairs on 128^2 random fields, training on the "
                          "GPU, flexible GMRES with the network vs the regularised + deflated method on held-out "
@@ -330,6 +339,14 @@ def main():
         return paper_sweeps(args)
     if args.paper_sinusoidal:
         return paper_sinusoidal(args)
+    if args.config5:
+        return config5_budget(args)
+    if args.config3:
+        import torch
+
+        from paper_1104_4263_gb300 import die, workloads as W
+        print(json.dumps({"config3": config3_rates(die, W, torch)}))
+        return 0
 
     import numpy as np
     import torch
@@ -353,6 +370,9 @@ def main():
     t0 = time.perf_counter()
     op = die.Operator(p.eps_r, p.h)
     t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tune = op.autotune(force=True)         # tile height of the complex64 row passes
+    tune["seconds"] = time.perf_counter() - t0
     b = op.plane_wave(replicas.angle_for_rank(rank))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -419,7 +439,9 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "grid": [p.n1, p.n2], "unknowns": 2 * p.N, "restart": RESTART,
                       "deflated": D.r, "step_arnoldi_steps": args.step_iters,
-                      "parallelism": f"replicas x{world} (one incidence angle per GPU)", "l2": L2_NOTE}}
+                      "parallelism": f"replicas x{world} (one incidence angle per GPU)", "l2": L2_NOTE,
+                      "tile_rows": tune["tile_rows"]}}
+    out["autotune"] = tune
     out["e2e"] = {"value": e2e_units / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes}
     # library kernels per step (counted in the identical profiled steps) x timed steps
@@ -492,10 +514,10 @@ def main():
                                   "us_per_product": mv["us_per_product"],
                                   "note": "L2 flushed before each product; CUDA events on the launching stream"}
     _extra(out, "fp64_same_budget", lambda: fp64_same_budget(op, b, args.step_iters, dt / args.steps, torch))
-    _extra(out, "batch_solve", lambda: [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)])
-    _extra(out, "small_grids", lambda: small_grid_rates(die, W, torch))
-    _extra(out, "many_systems", lambda: many_rates(die, W, torch))
-    _extra(out, "config3", lambda: config3_rates(die, W, torch))
+    if not args.single_system:
+        _extra(out, "batch_solve", lambda: [batch_solve_rates(op, D, die, torch, nrhs=k) for k in (4, 8)])
+        _extra(out, "small_grids", lambda: small_grid_rates(die, W, torch))
+        _extra(out, "many_systems", lambda: many_rates(die, W, torch))
     if not args.no_compare:
         _extra(out, "plain_fp64_same_budget", lambda: plain_fp64(op, b, args.step_iters, dt / args.steps, last))
         _extra(out, "time_to_tol", lambda: time_to_tol(die, W, torch))
@@ -650,6 +672,7 @@ def small_grid_rates(die, W, torch, sizes=(64, 96, 128, 256, 512), iters: int = 
             continue
         q = probs[n]
         op = die.Operator(q.eps_r, q.h)
+        op.autotune()                      # per-size tile height (timed once per size)
         b = op.plane_wave(0.0)
         B = torch.stack([op.plane_wave(2 * math.pi * k / nrhs) for k in range(nrhs)]).contiguous()
         kw = dict(restart=RESTART, tol=1e-14, max_iters=iters, regularized=True, inner=die.DIE_FP32_INNER)
@@ -685,6 +708,7 @@ def many_rates(die, W, torch, count: int = 16, n_angles: int = 4, iters: int = 2
     ops, bs = [], []
     for q in probs:
         op = die.Operator(q.eps_r, q.h)
+        op.autotune()                      # per-size tile height (timed once per size)
         for j in range(n_angles):
             ops.append(op)
             bs.append(op.plane_wave(2 * math.pi * j / n_angles))
@@ -809,6 +833,7 @@ def config3_rates(die, W, torch, tol: float = 1e-6, max_iters: int = 3000):
     ops, bs = [], []
     for q in probs:
         op = die.Operator(q.eps_r, q.h)
+        op.autotune()                      # per-size tile height (timed once per size)
         for psi in q.psi:
             ops.append(op)
             bs.append(op.plane_wave(psi))
@@ -1079,6 +1104,75 @@ def paper_sinusoidal(args, tol: float = 1e-8, max_iters: int = 60000):
         "speedup_online": ta / tp if tp > 0 else None, "speedup_with_build": ta / (tp + tb),
         "paper": {"A_s": 162692, "ARAP_s": 11620, "eigs_s": 775, "speedup_online": 14.0, "speedup_with_build": 13.1},
         "tol": tol}}))
+    return 0
+
+
+def config5_budget(args, r: int = 40, restart: int = 40):
+    """The large composite: 400 seeded cylinders (radius 0.2-0.6 wavelength, eps_r in
+    {-6 + 0.5i, 2, 9, 30 + 1i}) on a 2048^2 grid of side 32 wavelengths (8.4 M unknowns).
+    Plain FP64 GMRES(40) and, under Section 5's memory rule, GMRES(40 + r) on A, against
+    A_R A P^-1 with the r = 40 largest-magnitude eigenvalues deflated, GMRES(40), with FP64
+    products and with complex64 products (FP64 Krylov and restarts), each for `--budget`
+    Arnoldi steps toward 1e-6.  Reported: residual of the solved system at marked steps,
+    seconds, and the steps and seconds each form needs to reach the residual plain FP64
+    GMRES(40) ends at."""
+    import numpy as np
+    import torch
+
+    from paper_1104_4263_gb300 import die, workloads as W
+    budget = args.budget
+    marks = [m for m in (100, 300, 1000, 2000, 5000) if m <= budget]
+    t0 = time.perf_counter()
+    p = W.random_cylinders()
+    t_gen = time.perf_counter() - t0
+    op = die.Operator(p.eps_r, p.h)
+    b = op.plane_wave(0.0)
+    out = {"grid": [p.n1, p.n2], "unknowns": 2 * p.N, "cylinders": 400, "tol": TOL, "budget_steps": budget,
+           "restart": restart, "input_seconds": t_gen}
+    builds = {}
+    for name, inner in (("fp32_inner", die.DIE_FP32_INNER), ("fp64", die.DIE_FP64)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D = die.Deflation(op, r, tol=1e-4, regularized=True, inner=inner)
+        torch.cuda.synchronize()
+        builds[name] = (D, time.perf_counter() - t0)
+    out["deflation_build_s"] = {k: v[1] for k, v in builds.items()}
+    out["deflation_converged"] = {k: v[0].converged for k, v in builds.items()}
+    runs = (("plain_fp64", dict(restart=restart)),
+            ("plain_fp64_fair_memory", dict(restart=restart + r)),
+            ("reg_defl_fp64", dict(restart=restart, regularized=True, deflation=builds["fp64"][0])),
+            ("reg_defl_mixed", dict(restart=restart, regularized=True, deflation=builds["fp32_inner"][0],
+                                    inner=die.DIE_FP32_INNER)))
+    hist = {}
+    for name, kw in runs:
+        op.solve(b, tol=TOL, **dict(kw, max_iters=kw["restart"]))   # context allocated, kernels warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = op.solve(b, tol=TOL, max_iters=budget, history=budget, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h = np.asarray(rep["history"])
+        hist[name] = (h, dt)
+        out[name] = {"restart": kw["restart"], "seconds": dt, "iters": rep["iters"], "converged": rep["converged"],
+                     "rel_res_solved": rep["rel_res_solved"], "rel_res_orig": rep["rel_res_orig"],
+                     "ms_per_step": 1e3 * dt / max(rep["iters"], 1), "n_reorth": rep["n_reorth"],
+                     "history": {m: float(h[m - 1]) for m in marks if m <= len(h)}}
+    target = float(hist["plain_fp64"][0][-1])
+    out["plain_fp64_final_residual"] = target
+    for name, (h, dt) in hist.items():
+        hit = np.nonzero(h <= target)[0]
+        if hit.size:
+            steps = int(hit[0]) + 1
+            out[name]["steps_to_plain_final"] = steps
+            out[name]["seconds_to_plain_final"] = dt * steps / len(h)
+    base = out["plain_fp64"].get("seconds_to_plain_final")
+    for name in hist:
+        s_ = out[name].get("seconds_to_plain_final")
+        if base and s_:
+            out[name]["speedup_to_plain_final"] = base / s_
+    out["note"] = ("seconds_to_plain_final = the solve's seconds x the fraction of its steps taken until its "
+                   "residual first reached plain FP64 GMRES(40)'s final residual; the deflation build is extra")
+    print(json.dumps({"config5": out}))
     return 0
 
 

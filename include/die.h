@@ -104,6 +104,35 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
  * DIE_EINVAL, DIE_ESINGULAR, DIE_ENOMEM, DIE_ECUDA. */
 die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_device, void* stream);
 
+/* Schedule of the complex64 products: the tile height (rows per block) of the row passes
+ * (contrast multiply + row FFT, row inverse FFT + crop, and the fused pass of the
+ * regularised product, Eq. (4.1)) on grids whose row FFT is the compile-time path
+ * (M1 = 2 n1 = 2^a, 256 <= M1 <= 4096); other grids have one schedule.  Candidate heights
+ * are 1, 2, 4 and 8 rows (at most 512 threads per block: M1 = 2048 allows up to 4, 4096
+ * up to 2; the default is 4, 2 at M1 = 4096).  Every height gives bit-identical products.
+ *
+ * dieop_autotune times the complex64 regularised product A(chi') A(chi) at every
+ * candidate height (CUDA events on `stream`, 3 warm-up and 20 timed products each, on
+ * two 2 n1 n2 complex64 scratch vectors it allocates and frees) and keeps the default
+ * unless another height is at least 3% faster, then the fastest (the timed product stands
+ * in for the solver's passes, whose deflated first row pass may rank close heights
+ * differently).
+ * The choice is remembered per (device, M1, n2) for the process: a later call on an
+ * operator of the same sizes reuses it without timing unless force != 0.  tile_rows
+ * (host, may be NULL) receives the height used; us4 (host, may be NULL) receives the
+ * microseconds per product at heights 1, 2, 4, 8 (0: not a candidate or not timed this
+ * call).  Not concurrent with other calls on the operator (it uses the operator's
+ * workspace).  Synchronises the stream.  Errors: DIE_EINVAL, DIE_ENOMEM, DIE_ECUDA. */
+die_status dieop_autotune(dieop_t op, int force, void* stream, int* tile_rows, double* us4);
+
+/* Sets the tile height (0 = the default; 1, 2, 4 or 8 where the grid allows it) and
+ * returns DIE_EINVAL for any other value or a grid with one schedule.  Affects products
+ * launched afterwards (a CUDA graph captured before keeps the height it captured). */
+die_status dieop_set_tile_rows(dieop_t op, int tile_rows);
+
+/* The tile height the complex64 row passes use (0 for a grid with one schedule). */
+int dieop_tile_rows(dieop_t op);
+
 /* Actual sizes chosen at create: out[0..5] = n1, n2, M1, M2, N = n1*n2, prec. */
 die_status dieop_info(dieop_t op, long long* out6);
 

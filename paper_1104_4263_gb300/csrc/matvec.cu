@@ -1,5 +1,7 @@
 // FP64 instantiations of the product kernels (matvec_kernels.cuh) and the operator views.
-#include "matvec_kernels.cuh"
+#include "rows_fast.cuh"
+
+DIE_INSTANTIATE_ROWS_C128
 
 namespace die {
 
@@ -9,6 +11,7 @@ OpDev<double> view_d(const dieop_s* op) {
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_d; v.tw2 = op->tw2_d; v.gq = op->gq_d;
     v.twx1 = op->tw1_d + op->M1; v.twx2 = op->tw2_d + op->M2;
+    v.tr = 0;
     v.xs = 2L * op->n1 * op->n2;
     v.ws = 2L * op->M1 * op->n2;
     return v;
@@ -19,6 +22,7 @@ OpDev<float> view_f(const dieop_s* op) {
     v.f1 = op->f1; v.i1 = op->i1; v.f2 = op->f2; v.i2 = op->i2;
     v.tw1 = op->tw1_f; v.tw2 = op->tw2_f; v.gq = op->gq_f;
     v.twx1 = op->tw1_f + op->M1; v.twx2 = op->tw2_f + op->M2;
+    v.tr = op->tile_rows_c64;
     v.xs = 2L * op->n1 * op->n2;
     v.ws = 2L * op->M1 * op->n2;
     return v;

@@ -1,7 +1,9 @@
 // Complex64-arithmetic instantiations of the product kernels (matvec_kernels.cuh):
 // complex64 I/O (dieop_apply with DIE_FP32_INNER) and complex128 I/O (products inside
 // the FP32-inner GMRES cycles).
-#include "matvec_kernels.cuh"
+#include "rows_fast.cuh"
+
+DIE_INSTANTIATE_ROWS_C64(0)
 
 namespace die {
 
@@ -35,9 +37,7 @@ die_status apply_defl_xy(dieop_s* op, const DeflIn& d, float2* z, double2* y, bo
         return DIE_EINVAL;
     float2* W = reinterpret_cast<float2*>(ws->W);
     float2* vb = reinterpret_cast<float2*>(ws->v);
-#define K1D_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k1_defl_fast<LSV>, a_, rows_launch_fast<float2, LSV>(v.n2), st, v, d, op->chi_f, z, W, skip); }
-    DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1D_CASE));
-#undef K1D_CASE
+    with_tile_rows(v, [&](auto tr) { rows_defl_fast<decltype(tr)::value>(v, d, op->chi_f, z, W, skip, st); });
     launch_k2<float>(v, W, skip, st);
     if (reg) {
         launch_k3k1<float, float2>(v, W, z, op->chir_f, vb, skip, st);

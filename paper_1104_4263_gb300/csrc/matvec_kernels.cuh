@@ -26,6 +26,7 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 
 #include "fft_fast.cuh"
 #include "op.cuh"
@@ -36,7 +37,6 @@ namespace die {
 // Rows per block of the row passes: enough for 32-byte segments in the transposed
 // accesses (4 complex64 / 2 complex128), at most 512 threads per block.
 template <typename C> constexpr int tile_rows() { return sizeof(C) == 8 ? 4 : 2; }
-constexpr int kRowsMaxThreads = 512;
 constexpr size_t kStageGreenMaxSmem = 200 * 1024;
 
 template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
@@ -366,11 +366,11 @@ __device__ __forceinline__ void tile_io(C* tile, C* __restrict__ W, int c, int i
     }
 }
 
-template <typename T, typename IO, int L>
+template <typename T, typename IO, int L, int TR>
 __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict__ u, const C_t<T>* __restrict__ chi,
                                                C_t<T>* __restrict__ W, const int* __restrict__ skip) {
     using C = C_t<T>;
-    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    constexpr int G = L / 16, n1 = L / 2;
     using F0 = typename PlanStage<C, L, false, 0>::St;
     pdl_wait();
     if (block_flag(skip)) return;
@@ -404,12 +404,12 @@ __global__ void __launch_bounds__(512) k1_fast(OpDev<T> op, const IO* __restrict
 // z = v + sum_i V32_i cf_i (v = w / ||w|| written back to the FP64 Arnoldi vector, or
 // the complex64 x), stored to zout for the later passes, then chi * z and the forward
 // row transform as in k1_fast.  The basis loads go five vectors (40 loads) at a time.
-template <int L>
+template <int L, int TR>
 __global__ void __launch_bounds__(512) k1_defl_fast(OpDev<float> op, DeflIn d, const float2* __restrict__ chi,
                                                     float2* __restrict__ zout, float2* __restrict__ W,
                                                     const int* __restrict__ skip) {
     using C = float2;
-    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    constexpr int G = L / 16, n1 = L / 2;
     using F0 = typename PlanStage<C, L, false, 0>::St;
     __shared__ float2 cs[32];
     pdl_wait();
@@ -670,11 +670,11 @@ __global__ void __launch_bounds__(L / 16, (L == 1024 ? 7 : 1)) k2_fast2(OpDev<T>
     }
 }
 
-template <typename T, typename U, typename IO, int L>
+template <typename T, typename U, typename IO, int L, int TR>
 __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __restrict__ W, const U* __restrict__ u,
                                                IO* __restrict__ y, const int* __restrict__ skip) {
     using C = C_t<T>;
-    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2, ns = P2<L>::inv.ns;
+    constexpr int G = L / 16, n1 = L / 2, ns = P2<L>::inv.ns;
     using IL = typename PlanStage<C, L, true, ns - 1>::St;
     pdl_wait();
     if (block_flag(skip)) return;
@@ -706,12 +706,12 @@ __global__ void __launch_bounds__(512) k3_fast(OpDev<T> op, const C_t<T>* __rest
     }
 }
 
-template <typename T, typename IO, int L>
+template <typename T, typename IO, int L, int TR>
 __global__ void __launch_bounds__(512) k3k1_fast(OpDev<T> op, C_t<T>* __restrict__ W, const IO* __restrict__ u,
                                                  const C_t<T>* __restrict__ chir, C_t<T>* __restrict__ vbuf,
                                                  const int* __restrict__ skip) {
     using C = C_t<T>;
-    constexpr int G = L / 16, TR = fast_tr<C, L>(), n1 = L / 2;
+    constexpr int G = L / 16, n1 = L / 2;
     constexpr int nsi = P2<L>::inv.ns, nsf = P2<L>::fwd.ns;
     using IL = typename PlanStage<C, L, true, nsi - 1>::St;
     using F0 = typename PlanStage<C, L, false, 0>::St;
@@ -819,8 +819,7 @@ template <typename T> inline bool fast_rows(const OpDev<T>& v) {
 template <typename T> inline bool fast_cols(const OpDev<T>& v) {
     return 2 * v.n2 == v.M2 && v.M2 >= 256 && v.M2 <= 4096 && (v.M2 & (v.M2 - 1)) == 0;
 }
-template <typename C, int L> inline Launch rows_launch_fast(int n2) {
-    constexpr int TR = fast_tr<C, L>();
+template <typename C, int L, int TR> inline Launch rows_launch_fast(int n2) {
     return Launch{dim3((n2 + TR - 1) / TR, 2), dim3(TR * (L / 16)), (size_t)TR * tile_stride_c<L>() * sizeof(C)};
 }
 
@@ -834,14 +833,49 @@ template <typename C, int L> inline Launch rows_launch_fast(int n2) {
         default: break;               \
     }
 
+// Tile height of the fast row passes: the rows of one block (TR).  0 selects fast_tr,
+// the default of the element type and length; an operator's schedule (dieop_autotune,
+// dieop_set_tile_rows) may pick another valid height for its complex64 passes.  Every row
+// is transformed by the same threads and stages whatever TR is, so the products are
+// bit-identical for all heights.
+template <typename C, int L, int TR> constexpr int tile_of() { return TR == 0 ? fast_tr<C, L>() : TR; }
+template <typename C, int L, int TR> constexpr bool tile_ok() {
+    return TR == 0 || (TR * (L / 16) <= kRowsMaxThreads && TR != fast_tr<C, L>());
+}
+
+// The fast row passes at one tile height (definitions in rows_fast.cuh).
+template <typename T, typename IO, int TR>
+void rows_fwd_fast(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st,
+                   int nb);
+template <typename T, typename U, typename IO, int TR>
+void rows_inv_fast(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st, int nb);
+template <typename T, typename IO, int TR>
+void rows_inv_fwd_fast(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
+                       cudaStream_t st, int nb);
+template <int TR>
+void rows_defl_fast(const OpDev<float>& v, const DeflIn& d, const float2* chi, float2* z, float2* W, const int* skip,
+                    cudaStream_t st);
+
+// Calls F<TR> with the tile height of the view (complex64: the operator's schedule).
+template <typename T, typename F>
+inline void with_tile_rows(const OpDev<T>& v, F&& f) {
+    if constexpr (sizeof(C_t<T>) == 8) {
+        switch (tile_rows_code(v.tr, v.M1)) {
+            case 1: f(std::integral_constant<int, 1>{}); return;
+            case 2: f(std::integral_constant<int, 2>{}); return;
+            case 8: f(std::integral_constant<int, 8>{}); return;
+            default: break;
+        }
+    }
+    f(std::integral_constant<int, 0>{});
+}
+
 // nb > 1: a batched product over nb right-hand sides (grid z: row passes, grid y: columns).
 template <typename T, typename IO>
 inline void launch_k1(const OpDev<T>& v, const IO* u, const C_t<T>* chi, C_t<T>* W, const int* skip, cudaStream_t st,
                       int nb = 1) {
     if (fast_rows(v)) {
-#define K1F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, u, chi, W, skip); }
-        DIE_PROF(PK_ROWS_FWD, st, DIE_FAST_SWITCH(v.M1, K1F_CASE));
-#undef K1F_CASE
+        with_tile_rows(v, [&](auto tr) { rows_fwd_fast<T, IO, decltype(tr)::value>(v, u, chi, W, skip, st, nb); });
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);
@@ -885,9 +919,7 @@ template <typename T, typename U, typename IO>
 inline void launch_k3(const OpDev<T>& v, const C_t<T>* W, const U* u, IO* y, const int* skip, cudaStream_t st,
                       int nb = 1) {
     if (fast_rows(v)) {
-#define K3F_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3_fast<T, U, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, y, skip); }
-        DIE_PROF(PK_ROWS_INV, st, DIE_FAST_SWITCH(v.M1, K3F_CASE));
-#undef K3F_CASE
+        with_tile_rows(v, [&](auto tr) { rows_inv_fast<T, U, IO, decltype(tr)::value>(v, W, u, y, skip, st, nb); });
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);
@@ -904,9 +936,9 @@ template <typename T, typename IO>
 inline void launch_k3k1(const OpDev<T>& v, C_t<T>* W, const IO* u, const C_t<T>* chir, C_t<T>* vb, const int* skip,
                         cudaStream_t st, int nb = 1) {
     if (fast_rows(v)) {
-#define KKF_CASE(LSV) { static std::atomic<bool> a_{false}; launch_kernel(k3k1_fast<T, IO, LSV>, a_, with_z(rows_launch_fast<C_t<T>, LSV>(v.n2), nb), st, v, W, u, chir, vb, skip); }
-        DIE_PROF(PK_ROWS_INV_FWD, st, DIE_FAST_SWITCH(v.M1, KKF_CASE));
-#undef KKF_CASE
+        with_tile_rows(v, [&](auto tr) {
+            rows_inv_fwd_fast<T, IO, decltype(tr)::value>(v, W, u, chir, vb, skip, st, nb);
+        });
         return;
     }
     const Launch l = with_z(rows_launch(v), nb);

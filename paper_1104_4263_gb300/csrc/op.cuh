@@ -19,7 +19,23 @@ struct OpDev {
     const C* gq;                  // quarter spectra of G11, G22, G12: [plane][k1q][k2q], pre-scaled
     long xs;                      // batched products: elements per field vector (2 n1 n2)
     long ws;                      // batched products: elements per set of row spectra (2 M1 n2)
+    int tr;                       // tile height of the fast row passes (0: default)
 };
+
+constexpr int kRowsMaxThreads = 512;    // threads per block of the row passes
+
+// Tile heights (rows per block) of the complex64 fast row passes, M1 = L: the default
+// (4 rows, or as many as 512 threads allow) and the alternatives with kernels of their own.
+constexpr int kTileRowsAlt[] = {1, 2, 8};
+inline int default_tile_rows_c64(int L) { return 4 * (L / 16) <= kRowsMaxThreads ? 4 : kRowsMaxThreads / (L / 16); }
+// The code the launchers use for height tr at length L: tr when it is a valid alternative,
+// else 0 (the default).
+inline int tile_rows_code(int tr, int L) {
+    if (tr <= 0 || tr == default_tile_rows_c64(L) || tr * (L / 16) > kRowsMaxThreads) return 0;
+    for (int a : kTileRowsAlt)
+        if (a == tr) return tr;
+    return 0;
+}
 
 struct Workspace {
     void* W = nullptr;            // 2 x M1 x n2 complex (compute precision), transposed row spectra
@@ -49,6 +65,7 @@ struct dieop_s {
     uint64_t id = 0;               // identity for deflation handles
     void* solver = nullptr;        // die::SolverCache, created by the first gmres_solve
     void* batch[16] = {};          // die::SolverCache of each right-hand side of gmres_solve_batch
+    int tile_rows_c64 = 0;         // tile height of the complex64 fast row passes (0: default)
 };
 
 namespace die {

@@ -71,6 +71,9 @@ EXPORTS = {
     "dieop_create": (ct.c_int, [ct.POINTER(Desc), ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "dieop_info": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
     "dieop_set_permittivity": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "dieop_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
+    "dieop_set_tile_rows": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "dieop_tile_rows": (ct.c_int, [ct.c_void_p]),
     "fno_encode_pair": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "dieop_apply_regularized": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -262,6 +265,23 @@ class Operator:
             raise ValueError("eps_r must have shape (n2, n1)")
         _check(_lib().dieop_set_permittivity(self._h, e.ctypes.data_as(ct.c_void_p), 0, _stream(stream)),
                "dieop_set_permittivity")
+
+    def autotune(self, force: bool = False, stream=None) -> dict:
+        """Time the complex64 regularised product at every tile height of the row passes
+        and keep the fastest (dieop_autotune); returns the height and the microseconds per
+        product at heights 1, 2, 4, 8 (0: not a candidate, or reused without timing)."""
+        tr = ct.c_int()
+        us = (ct.c_double * 4)()
+        _check(_lib().dieop_autotune(self._h, int(bool(force)), _stream(stream), ct.byref(tr), us), "dieop_autotune")
+        return {"tile_rows": tr.value, "us_per_product": {h: us[i] for i, h in enumerate((1, 2, 4, 8))}}
+
+    def set_tile_rows(self, rows: int):
+        """Tile height of the complex64 row passes: 0 (default), 1, 2, 4 or 8."""
+        _check(_lib().dieop_set_tile_rows(self._h, int(rows)), "dieop_set_tile_rows")
+
+    @property
+    def tile_rows(self) -> int:
+        return _lib().dieop_tile_rows(self._h)
 
     def close(self):
         if getattr(self, "_h", None):
