@@ -57,9 +57,7 @@ L2_NOTE = "working set > L2 (Krylov basis 31 x 8.4 MB, deflation basis 20 x 4.2 
 # 2N = 524288, from one capture of the committed profile driver (bench.py
 # --profile-driver; the kernel is unchanged since).  Its traffic grows with the vectors
 # read, so it is scaled to the bench's average launch by the algorithmic bytes.
-NCU_DOTS = {"dram_bytes": 175.310848e6 + 0.329984e6, "nv": 13, "n": 524288,
-            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:proj3 -s 10 -c 3 on "
-                      "bench.py --profile-driver (the 13-vector launch)"}
+NCU_DOTS = None     # DRAM bytes of one captured projection launch of the current kernel (set from a capture)
 
 
 def fp64_peak(die):
@@ -382,7 +380,7 @@ def main():
 
     def step(bb=b):
         return op.solve(bb, restart=RESTART, tol=TOL, max_iters=args.step_iters, regularized=True,
-                        inner=die.DIE_FP32_INNER, deflation=D)
+                        inner=die.DIE_FP32_INNER, deflation=D, graph=True)
 
     for _ in range(args.warmup):
         step()
@@ -440,7 +438,7 @@ def main():
            "config": {"workload": WORKLOAD, "grid": [p.n1, p.n2], "unknowns": 2 * p.N, "restart": RESTART,
                       "deflated": D.r, "step_arnoldi_steps": args.step_iters,
                       "parallelism": f"replicas x{world} (one incidence angle per GPU)", "l2": L2_NOTE,
-                      "tile_rows": tune["tile_rows"]}}
+                      "tile_rows": tune["tile_rows"], "cycles": "CUDA graphs (gmres_opts.graph)"}}
     out["autotune"] = tune
     out["e2e"] = {"value": e2e_units / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes}
@@ -495,7 +493,7 @@ def main():
                                "traffic": None, "kernel": best, "algorithmic_flops_per_launch": per_launch,
                                "peak_source": (f"FP64 FMA probe of this run (die_fp64_peak, {fp64['sms']} SMs; "
                                                f"nominal {fp64['nominal_tflops']:.3f} TFLOP/s)")}
-            if best == "dots" and 2 * p.N == NCU_DOTS["n"]:
+            if best == "dots" and NCU_DOTS and 2 * p.N == NCU_DOTS["n"]:
                 _, tot_bytes = work_model("dots_bytes", p, op, D.r, RESTART, cycles, prof_products, fp64_products)
                 alg_bytes = tot_bytes / k["launches"]
                 captured_alg = (NCU_DOTS["nv"] * 24 + 16) * NCU_DOTS["n"]
@@ -813,7 +811,7 @@ def fp64_same_budget(op, b, step_iters, step_s, torch):
     tb = time.perf_counter() - t0
     t0 = time.perf_counter()
     _, rep = op.solve(b, restart=RESTART, tol=TOL, max_iters=step_iters, regularized=True, inner=die.DIE_FP64,
-                      deflation=D)
+                      deflation=D, graph=True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"arnoldi_steps": rep["iters"], "seconds": dt, "regularized_per_s": rep["iters"] / dt,
@@ -865,7 +863,7 @@ def plain_fp64(op, b, step_iters, step_s, last):
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, rep = op.solve(b, restart=RESTART, tol=TOL, max_iters=step_iters)
+    _, rep = op.solve(b, restart=RESTART, tol=TOL, max_iters=step_iters, graph=True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"arnoldi_steps": rep["iters"], "seconds": dt, "rel_res": rep["rel_res_solved"],

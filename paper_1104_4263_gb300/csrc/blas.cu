@@ -254,7 +254,7 @@ __device__ __forceinline__ void proj_group3_n(int cnt, const double2* V, const d
 }
 
 // FP64 projections in the three-multiplication form, kGroup3 vectors per pass.
-constexpr int kGroup3 = 6;
+constexpr int kGroup3 = 8;
 __global__ void __launch_bounds__(kRedThreads, 2) proj3_kernel(const double2* __restrict__ V,
                                                                const double* __restrict__ VM, long ldv, int nv,
                                                                const double2* __restrict__ w, long n, int with_norm,

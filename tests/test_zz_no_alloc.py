@@ -54,3 +54,22 @@ def test_noalloc_matches_deflation_apply_twice(r):
 def test_noalloc_rejects_null_arguments():
     lib = die.lib()
     assert lib.deflation_apply_noalloc(None, None, None, None) == 1
+
+
+def test_noalloc_rejects_rank_above_its_array():
+    """A rank-129 handle (deflation_build allows up to 256) is refused with DIE_EINVAL by
+    the no-allocation entry point, whose static array holds rank 128, and nothing is
+    written; the ordinary entry point serves it."""
+    n = 12
+    eps = W.core_shell(n, side=1.2, r_core=0.25, r_shell=0.5, eps_core=-2 + 0.1j, eps_shell=20 + 0.5j).eps_r
+    op = die.Operator(eps, 0.1)
+    D = die.Deflation(op, 129, tol=1e-6, regularized=True, krylov_dim=137, max_restarts=2)
+    assert D.r == 129
+    lib = die.lib()
+    x = torch.from_numpy(W.random_vector(W.rng_for(120, 129), n, n)).cuda()
+    z = torch.full_like(x, complex("nan"))
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.deflation_apply_noalloc(D.handle, ct.c_void_p(x.data_ptr()), ct.c_void_p(z.data_ptr()), stream) == 1
+    torch.cuda.synchronize()
+    assert torch.isnan(z.real).all()
+    assert torch.isfinite(D.apply(x).real).all()
