@@ -57,7 +57,9 @@ L2_NOTE = "working set > L2 (Krylov basis 31 x 8.4 MB, deflation basis 20 x 4.2 
 # 2N = 524288, from one capture of the committed profile driver (bench.py
 # --profile-driver; the kernel is unchanged since).  Its traffic grows with the vectors
 # read, so it is scaled to the bench's average launch by the algorithmic bytes.
-NCU_DOTS = None     # DRAM bytes of one captured projection launch of the current kernel (set from a capture)
+NCU_DOTS = {"dram_bytes": 175.365632e6 + 0.137216e6, "nv": 13, "n": 524288,
+            "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:proj3 -s 10 -c 3 on "
+                      "bench.py --profile-driver (the 13-vector launch; groups of eight vectors)"}
 
 
 def fp64_peak(die):
@@ -587,8 +589,9 @@ def matvec_rates(op, p, die, torch):
         y = torch.empty_like(x)
         for _ in range(3):
             o.apply_regularized(x, y)
-        reps, ms = 20, 0.0
+        reps = 20
         s = torch.cuda.current_stream()
+        times = []
         for _ in range(reps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -596,14 +599,18 @@ def matvec_rates(op, p, die, torch):
             o.apply_regularized(x, y)
             e1.record(s)
             torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
+            times.append(e0.elapsed_time(e1))
+        # the median product: single products right after a flush vary by several percent
+        # (the flush leaves dirty lines that the product's accesses evict)
+        ms = reps * sorted(times)[reps // 2]
+        ms_mean = sum(times)
         if name == "c64":   # the same products batched over 8 right-hand sides (e.g. incidence angles)
             nb = 8
             xb = torch.randn(nb, 2, p.n2, p.n1, dtype=dt, device="cuda")
             yb = torch.empty_like(xb)
             for _ in range(3):
                 o.apply_batch(xb, yb, regularized=True)
-            msb = 0.0
+            tb = []
             for _ in range(reps):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -611,18 +618,20 @@ def matvec_rates(op, p, die, torch):
                 o.apply_batch(xb, yb, regularized=True)
                 e1.record(s)
                 torch.cuda.synchronize()
-                msb += e0.elapsed_time(e1)
+                tb.append(e0.elapsed_time(e1))
+            msb = reps * sorted(tb)[reps // 2]
             nbytes_b = nb * sum(product_bytes(p, o, 8).values())
             out["c64_batch8"] = {"regularized_per_s": nb * reps / (msb / 1e3), "us_per_product": 1e3 * msb / reps / nb,
                                  "GBps": nbytes_b / (msb / reps / 1e3) / 1e9,
                                  "hbm_frac": nbytes_b / (msb / reps / 1e3) / 1e9 / hbm_peak(),
-                                 "note": "8 right-hand sides per call (dieop_apply_batch), L2 flushed before each call"}
+                                 "note": "8 right-hand sides per call (dieop_apply_batch), L2 flushed before each call; median of 20"}
         s_el = 8 if name == "c64" else 16
         nbytes = sum(product_bytes(p, o, s_el).values())
         gbs = nbytes / (ms / reps / 1e3) / 1e9
         out[name] = {"regularized_per_s": reps / (ms / 1e3), "us_per_product": 1e3 * ms / reps,
+                     "us_per_product_mean": 1e3 * ms_mean / reps,
                      "algorithmic_bytes": nbytes, "GBps": gbs, "hbm_frac": gbs / hbm_peak(),
-                     "l2": "flushed (256 MB write) before each product"}
+                     "l2": "flushed (256 MB write) before each product; median of 20 products"}
     return out
 
 
