@@ -29,6 +29,10 @@ preconditioning", that it follows):
   cylinder   -- closed-form series for TE scattering by a homogeneous circular
                 cylinder (textbook separation of variables in the Maxwell system
                 of Eq. (2.1)); a pin for the discretisation.
+  tm         -- the scalar TM operator of Section 2 and its cylinder series.
+  te_mag     -- the TE system with magnetic contrast, unknowns (E1, E2, H3): the
+                couplings of Section 3's compact kernels, the regulariser
+                A(chi'_e, chi_m), and the magneto-dielectric cylinder series.
 
 Everything is complex128 / float64.  Parity status: every function here is pinned
 by `tests/test_oracle_*.py` against closed forms, invariants or brute force; none
