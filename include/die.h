@@ -18,7 +18,9 @@
  * FFT convolution (Sections 1 and 5).
  *
  * Vector layout.  A field vector is 2 * n1 * n2 interleaved complex numbers in
- * the order [component][x2][x1] (x1 fastest): E1 plane, then E2 plane.
+ * the order [component][x2][x1] (x1 fastest): E1 plane, then E2 plane.  For the
+ * polarisation DIE_TE_MAG it is 3 * n1 * n2: E1, E2, then H3.  Wherever a size below
+ * says "2 n1 n2", read "3 n1 n2" for DIE_TE_MAG.
  * Complex128 = two doubles (re, im); complex64 = two floats.
  *
  * Conventions for every call:
@@ -65,10 +67,23 @@ typedef enum die_precision {
  * two-plane layout below with E3 in the first plane and a zero second plane: the TM
  * operator acts on each plane separately (the off-diagonal kernel plane is zero), so a zero
  * second plane stays zero through every product, solve and deflation; the products cost
- * what a TE product costs. */
+ * what a TE product costs.
+ * DIE_TE_MAG: the full TE system with electric and magnetic contrast, unknowns
+ * (E1, E2, H3) of Eq. (2.12) in three planes, A = I - G X, X = diag(chi_e, chi_e, chi_m),
+ * chi_e = eps_r - 1, chi_m = mu_r - 1 (mu_r from dieop_set_permeability; 1 until then).
+ * Besides the electric block of Eqs. (4.3)-(4.5), G has the couplings of Section 3's
+ * compact kernels K13, K23, K31, K32, K33 (eps_b = mu_b = 1, omega = k_b):
+ * G13 = G31 = (k_b^2 h^2 / 4) H1(k_b r) theta_2, G23 = G32 = -(k_b^2 h^2 / 4) H1(k_b r) theta_1,
+ * G33 = k_b^2 h^2 (i/4) H0(k_b r), zero at r = 0 except G33(0) = (i pi/2) k_b a H1(k_b a) - 1
+ * (the [A33]_nn of Section 4).  (The discrete relations A31 = -A13, A23 = -A32 printed in
+ * Section 4 disagree with K31, K32 and are not used.)  The regulariser is A(chi'_e, chi_m),
+ * chi'_e = 1/eps_r - 1: the symbol I + chi_e Q of Section 3 does not involve chi_m.  Its
+ * products run on the runtime-plan kernels (no compile-time FFT path, no tile schedule, no
+ * complex64 deflated first pass), and the learned preconditioner does not take it. */
 typedef enum die_polarization {
     DIE_TE = 0,
-    DIE_TM = 1
+    DIE_TM = 1,
+    DIE_TE_MAG = 2
 } die_polarization;
 
 typedef struct dieop_s* dieop_t;
@@ -82,7 +97,7 @@ typedef struct dieop_desc {
     double k_b;            /* background wavenumber; <= 0 selects 2 pi                         */
     die_precision prec;    /* element type of dieop_apply / dieop_apply_regularized I/O        */
     int M1, M2;            /* FFT sizes, 0 = smallest 2^a 3^b >= 2 n; else >= 2 n and 2^a 3^b */
-    die_polarization pol;  /* DIE_TE (default, 0) or DIE_TM                                    */
+    die_polarization pol;  /* DIE_TE (default, 0), DIE_TM or DIE_TE_MAG                         */
 } dieop_desc;
 
 /* dieop_create -- build the operator of Eqs. (4.3)-(4.5) for a permittivity map.
@@ -103,6 +118,13 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
  * before the call are rejected by the solves.  Synchronises the stream.  Errors:
  * DIE_EINVAL, DIE_ESINGULAR, DIE_ENOMEM, DIE_ECUDA. */
 die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_device, void* stream);
+
+/* Sets the relative permeability map of a DIE_TE_MAG operator: chi_m = mu_r - 1 (Eq. (2.13)).
+ * mu_r: n1*n2 interleaved complex128, host (mu_on_device = 0) or device.  DIE_EINVAL for
+ * another polarisation, DIE_ENAN for a non-finite value (the operator keeps its previous
+ * map).  The operator gets a new identity, as for dieop_set_permittivity.  Synchronises
+ * the stream.  Errors: DIE_EINVAL, DIE_ENAN, DIE_ENOMEM, DIE_ECUDA. */
+die_status dieop_set_permeability(dieop_t op, const void* mu_r, int mu_on_device, void* stream);
 
 /* Schedule of the complex64 products: the tile height (rows per block) of the row passes
  * (contrast multiply + row FFT, row inverse FFT + crop, and the fused pass of the
@@ -162,7 +184,8 @@ die_status dieop_apply_batch(dieop_t op, int nrhs, const void* x, void* y, int r
 
 /* b = incident TE plane wave of unit |E| at angle psi to the x1 axis (Section 4, end):
  * H3 = exp(i k_b (x1 cos psi + x2 sin psi)), E1 = -sin(psi) H3, E2 = cos(psi) H3; for a
- * TM operator E3 = exp(i k_b (x1 cos psi + x2 sin psi)) in the first plane, 0 in the second.
+ * TM operator E3 = exp(i k_b (x1 cos psi + x2 sin psi)) in the first plane, 0 in the second;
+ * for DIE_TE_MAG (E1, E2, H3) in three planes, as for TE.
  * b: device, 2*n1*n2 complex128.  Errors: DIE_EINVAL, DIE_ECUDA. */
 die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream);
 

@@ -33,6 +33,8 @@ bool pdl_enabled() {
 
 die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st);
 die_status compute_contrasts(dieop_s* op, const double2* eps_dev, cudaStream_t st);
+die_status compute_magnetic_contrast(const dieop_s* op, const double2* mu_dev, double2* chim_d, float2* chim_f,
+                                     int* flag, cudaStream_t st);
 die_status compute_contrasts_into(const dieop_s* op, const double2* eps_dev, double2* chi_d, double2* chir_d,
                                   float2* chi_f, float2* chir_f, int* flag, cudaStream_t st);
 
@@ -121,7 +123,8 @@ using namespace die;
 static void free_op(dieop_s* op) {
     if (!op) return;
     void* ptrs[] = {op->tw1_d, op->tw2_d, op->tw1_f, op->tw2_f, op->gq_d, op->gq_f, op->chi_d, op->chir_d,
-                    op->chi_f, op->chir_f, op->ws.W, op->ws.v, op->wsb.W, op->wsb.v, op->dflag};
+                    op->chi_f, op->chir_f, op->chim_d, op->chim_f, op->ws.W, op->ws.v, op->wsb.W, op->wsb.v,
+                    op->dflag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_solver_cache(op);
@@ -141,7 +144,7 @@ static std::map<std::tuple<int, int, int>, int> g_sched;
 
 static bool has_tile_schedule(const dieop_s* op) {
     const int L = op->M1;
-    return 2 * op->n1 == L && L >= 256 && L <= 4096 && (L & (L - 1)) == 0;
+    return op->planes == 2 && 2 * op->n1 == L && L >= 256 && L <= 4096 && (L & (L - 1)) == 0;
 }
 // Height t (1, 2, 4, 8) -> stored code (0 for the default), or -1 if t is not a candidate.
 static int tile_code_of(const dieop_s* op, int t) {
@@ -187,7 +190,7 @@ die_status dieop_autotune(dieop_t op, int force, void* stream, int* tile_rows, d
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = 2 * (size_t)op->N * sizeof(float2);
+    const size_t bytes = (size_t)vec_len(op) * sizeof(float2);
     float2 *x = nullptr, *y = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const int saved = op->tile_rows_c64;
@@ -272,6 +275,7 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     op->k = desc->k_b > 0 ? desc->k_b : 6.283185307179586476925286766559;
     op->prec = desc->prec;
     op->pol = desc->pol;
+    op->planes = desc->pol == DIE_TE_MAG ? 3 : 2;
     op->M1 = desc->M1 > 0 ? desc->M1 : choose_fft_size(desc->n1);
     op->M2 = desc->M2 > 0 ? desc->M2 : choose_fft_size(desc->n2);
     if (op->M1 < 2 * op->n1 || op->M2 < 2 * op->n2) return DIE_EINVAL;
@@ -287,14 +291,21 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     DIE_TRY(dmalloc(&op->tw2_d, 3 * (size_t)op->M2 * sizeof(double2)));
     DIE_TRY(dmalloc(&op->tw1_f, 3 * (size_t)op->M1 * sizeof(float2)));
     DIE_TRY(dmalloc(&op->tw2_f, 3 * (size_t)op->M2 * sizeof(float2)));
-    DIE_TRY(dmalloc(&op->gq_d, 3 * q * sizeof(double2)));
-    DIE_TRY(dmalloc(&op->gq_f, 3 * q * sizeof(float2)));
+    const int ng = green_plane_count(op);
+    DIE_TRY(dmalloc(&op->gq_d, ng * q * sizeof(double2)));
+    DIE_TRY(dmalloc(&op->gq_f, ng * q * sizeof(float2)));
     DIE_TRY(dmalloc(&op->chi_d, N * sizeof(double2)));
     DIE_TRY(dmalloc(&op->chir_d, N * sizeof(double2)));
     DIE_TRY(dmalloc(&op->chi_f, N * sizeof(float2)));
     DIE_TRY(dmalloc(&op->chir_f, N * sizeof(float2)));
-    op->ws.W_bytes = 2 * (size_t)op->M1 * op->n2 * sizeof(double2);
-    op->ws.v_bytes = 2 * (size_t)N * sizeof(double2);
+    if (op->planes == 3) {         // chi_m = 0 (mu_r = 1) until dieop_set_permeability
+        DIE_TRY(dmalloc(&op->chim_d, N * sizeof(double2)));
+        DIE_TRY(dmalloc(&op->chim_f, N * sizeof(float2)));
+        DIE_CUDA_TRY(cudaMemsetAsync(op->chim_d, 0, N * sizeof(double2), st));
+        DIE_CUDA_TRY(cudaMemsetAsync(op->chim_f, 0, N * sizeof(float2), st));
+    }
+    op->ws.W_bytes = (size_t)op->planes * op->M1 * op->n2 * sizeof(double2);
+    op->ws.v_bytes = (size_t)op->planes * N * sizeof(double2);
     DIE_TRY(dmalloc(&op->ws.W, op->ws.W_bytes));
     DIE_TRY(dmalloc(&op->ws.v, op->ws.v_bytes));
     DIE_TRY(dmalloc(&op->dflag, sizeof(int)));
@@ -311,11 +322,11 @@ static die_status create_impl(const dieop_desc* desc, const void* eps_r, int eps
     DIE_CUDA_TRY(cudaMemcpyAsync(op->tw2_f, t2f.data(), t2f.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
 
     double2* scratch = nullptr;
-    const size_t scratch_bytes = 3 * (size_t)op->M1 * op->M2 * sizeof(double2) + (eps_on_device ? 0 : N * sizeof(double2));
+    const size_t scratch_bytes = ng * (size_t)op->M1 * op->M2 * sizeof(double2) + (eps_on_device ? 0 : N * sizeof(double2));
     DIE_TRY(dmalloc(&scratch, scratch_bytes));
     const double2* eps_dev = (const double2*)eps_r;
     if (!eps_on_device) {
-        double2* e = scratch + 3 * (size_t)op->M1 * op->M2;
+        double2* e = scratch + ng * (size_t)op->M1 * op->M2;
         die_status s = DIE_OK;
         if (cudaMemcpyAsync(e, eps_r, N * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess) s = DIE_ECUDA;
         if (s != DIE_OK) { cudaFree(scratch); return s; }
@@ -340,7 +351,7 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
     if (desc->n1 < 2 || desc->n2 < 2 || desc->n1 > 2048 || desc->n2 > 2048) return DIE_EINVAL;
     if (!(desc->h > 0) || !isfinite(desc->h)) return DIE_EINVAL;
     if (desc->prec != DIE_FP64 && desc->prec != DIE_FP32_INNER) return DIE_EINVAL;
-    if (desc->pol != DIE_TE && desc->pol != DIE_TM) return DIE_EINVAL;
+    if (desc->pol != DIE_TE && desc->pol != DIE_TM && desc->pol != DIE_TE_MAG) return DIE_EINVAL;
     dieop_s* op = new (std::nothrow) dieop_s();
     if (!op) return DIE_ENOMEM;
     die_status s;
@@ -396,6 +407,45 @@ die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_devi
     return DIE_OK;
 }
 
+die_status dieop_set_permeability(dieop_t op, const void* mu_r, int mu_on_device, void* stream) {
+    if (!op || !mu_r || op->planes != 3) return DIE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long N = op->N;
+    // new contrast into scratch first: the operator keeps its old one if mu_r is rejected
+    // layout: the FP64 contrast, the host map's copy (both double2, so 16-byte aligned at
+    // offsets 0 and 16 N), then the complex64 contrast and the flag
+    char* scratch = nullptr;
+    const size_t d_bytes = (size_t)N * sizeof(double2);
+    const size_t m_bytes = mu_on_device ? 0 : d_bytes;
+    const size_t bytes = d_bytes + m_bytes + (size_t)N * sizeof(float2) + sizeof(int);
+    if (cudaMalloc((void**)&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DIE_ENOMEM;
+    }
+    double2* cd = reinterpret_cast<double2*>(scratch);
+    const double2* m = mu_on_device ? (const double2*)mu_r : reinterpret_cast<const double2*>(scratch + d_bytes);
+    float2* cf = reinterpret_cast<float2*>(scratch + d_bytes + m_bytes);
+    int* flagd = reinterpret_cast<int*>(scratch + d_bytes + m_bytes + (size_t)N * sizeof(float2));
+    die_status s = DIE_OK;
+    int flag = 0;
+    if (!mu_on_device && cudaMemcpyAsync((void*)m, mu_r, N * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = DIE_ECUDA;
+    if (s == DIE_OK && cudaMemsetAsync(flagd, 0, sizeof(int), st) != cudaSuccess) s = DIE_ECUDA;
+    if (s == DIE_OK) s = compute_magnetic_contrast(op, m, cd, cf, flagd, st);
+    if (s == DIE_OK && (cudaMemcpyAsync(&flag, flagd, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        s = DIE_ECUDA;
+    if (s == DIE_OK && flag) s = DIE_ENAN;
+    if (s == DIE_OK &&
+        (cudaMemcpyAsync(op->chim_d, cd, N * sizeof(double2), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(op->chim_f, cf, N * sizeof(float2), cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+        s = DIE_ECUDA;
+    cudaFree(scratch);           // waits for the copies
+    if (s != DIE_OK) return s;
+    op->id = next_handle_id();   // deflation handles of the old contrast no longer match
+    return DIE_OK;
+}
+
 die_status dieop_info(dieop_t op, long long* o) {
     if (!op || !o) return DIE_EINVAL;
     o[0] = op->n1; o[1] = op->n2; o[2] = op->M1; o[3] = op->M2; o[4] = op->N; o[5] = op->prec;
@@ -436,8 +486,8 @@ die_status dieop_apply_batch(dieop_t op, int nrhs, const void* x, void* y, int r
         op->wsb = Workspace{};
         op->wsb_cap = 0;
         const size_t es = op->prec == DIE_FP64 ? sizeof(double2) : sizeof(float2);
-        op->wsb.W_bytes = (size_t)nrhs * 2 * op->M1 * op->n2 * es;
-        op->wsb.v_bytes = (size_t)nrhs * 2 * op->N * es;
+        op->wsb.W_bytes = (size_t)nrhs * op->planes * op->M1 * op->n2 * es;
+        op->wsb.v_bytes = (size_t)nrhs * op->planes * op->N * es;
         if (cudaMalloc(&op->wsb.W, op->wsb.W_bytes) != cudaSuccess ||
             cudaMalloc(&op->wsb.v, op->wsb.v_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -465,7 +515,8 @@ die_status dieop_apply_regularizer(dieop_t op, const void* x, void* y, void* str
 // source-free TE equations of Eq. (2.1) hold): H3 = exp(i k (x1 cos psi + x2 sin psi)),
 // E1 = -sin(psi) H3, E2 = cos(psi) H3, at cell centres x_i = (i + 1/2) h - n h / 2.
 // TM (tm != 0): E3 = exp(i k (x1 cos psi + x2 sin psi)) in the first plane, zero in the second.
-__global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi, int tm, double2* b) {
+// Three planes (mag != 0): (E1, E2, H3) as for TE, H3 in the third plane.
+__global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi, int tm, int mag, double2* b) {
     const long N = (long)n1 * n2;
     double sp, cp;
     sincos(psi, &sp, &cp);
@@ -481,6 +532,7 @@ __global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi
         } else {
             b[i] = make_double2(-sp * c, -sp * s);
             b[N + i] = make_double2(cp * c, cp * s);
+            if (mag) b[2 * N + i] = make_double2(c, s);
         }
     }
 }
@@ -488,7 +540,8 @@ __global__ void plane_wave_kernel(int n1, int n2, double h, double k, double psi
 extern "C" die_status dieop_rhs_plane_wave(dieop_t op, double psi, void* b, void* stream) {
     if (!op || !b || !isfinite(psi)) return DIE_EINVAL;
     plane_wave_kernel<<<608, 256, 0, (cudaStream_t)stream>>>(op->n1, op->n2, op->h, op->k, psi,
-                                                              op->pol == DIE_TM ? 1 : 0, (double2*)b);
+                                                              op->pol == DIE_TM ? 1 : 0, op->planes == 3 ? 1 : 0,
+                                                              (double2*)b);
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -168,7 +168,7 @@ struct KsWork {
 
 static die_status build_impl(dieop_s* op, const defl_opts* o, cudaStream_t st, defl_s* d, double* eig_out,
                              int* r_out) {
-    const long n = 2L * op->N;
+    const long n = vec_len(op);
     const bool reg = o->regularized != 0, mixed = o->inner == DIE_FP32_INNER;
     int r = o->r;
     int rmax = o->r_max > 0 ? o->r_max : 64;
@@ -332,7 +332,7 @@ extern "C" die_status deflation_build(dieop_t op, const defl_opts* o, void* stre
     if (o->r < 0 || o->r > kMaxDeflation || o->r_max > kMaxDeflation || o->krylov_dim < 0 || o->max_restarts < 0)
         return DIE_EINVAL;
     if (o->inner != DIE_FP64 && o->inner != DIE_FP32_INNER) return DIE_EINVAL;
-    if (o->r > 0 && 2L * op->N <= o->r + 2) return DIE_EINVAL;
+    if (o->r > 0 && vec_len(op) <= o->r + 2) return DIE_EINVAL;
     defl_s* d = new (std::nothrow) defl_s();
     if (!d) return DIE_ENOMEM;
     die_status s;

@@ -50,7 +50,7 @@ die_status norm2(FgmresWork& w, const double2* v, long n, cudaStream_t st, doubl
 die_status fgmres_impl(dieop_s* op, fno_s* net, const gmres_opts* o, const double2* b, double2* x,
                        gmres_report* rep, cudaStream_t st, bool* nan_out) {
     const int m = o->restart;
-    const long n = 2L * op->N;
+    const long n = vec_len(op);
     FgmresWork w;
     auto al = [](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
     if (!al((void**)&w.V, (size_t)(m + 1) * n * sizeof(double2)) || !al((void**)&w.Z, (size_t)m * n * sizeof(double2)) ||

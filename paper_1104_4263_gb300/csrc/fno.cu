@@ -704,7 +704,7 @@ die_status fno_apply_precond(fno_s* f, dieop_s* op, const double2* v, double2* z
 }
 
 bool fno_matches(const fno_s* f, const dieop_s* op) {
-    return f->cin == 6 && f->cout == 4 && f->H == op->n2 && f->W == op->n1;
+    return op->planes == 2 && f->cin == 6 && f->cout == 4 && f->H == op->n2 && f->W == op->n1;
 }
 }  // namespace die
 
@@ -716,7 +716,7 @@ extern "C" die_status fno_precondition(fno_t f, dieop_t op, const void* v, void*
 }
 
 extern "C" die_status fno_encode_pair(dieop_t op, const void* b, const void* u, float* x, float* t, void* stream) {
-    if (!op || !b || !x || (t && !u)) return DIE_EINVAL;
+    if (!op || !b || !x || (t && !u) || op->planes != 2) return DIE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const long N = op->N;
     double* ss = nullptr;

@@ -107,7 +107,7 @@ static int ints_count(int m) { return 8 + m; }
 // Buffers, streams and events of a new context for GMRES(m) with hist_cap history
 // entries; on failure the caller frees what was made (free_cache handles any subset).
 static die_status init_cache(SolverCache* c, dieop_s* op, int m, int hist_cap, bool own_ws) {
-    const long n = 2L * op->N;
+    const long n = vec_len(op);
     c->m_cap = m;
     c->n = n;
     c->hist_cap = hist_cap;
@@ -347,7 +347,7 @@ static die_status solve_ctx(dieop_s* op, defl_s* defl, const gmres_opts* o, cons
     const double eta = o->reorth_eta > 0 ? o->reorth_eta : default_reorth_eta(o->restart);
     const double eta2 = eta >= 1.0 ? 1.0 : eta * eta;
     const int m = o->restart;
-    const long n = 2L * op->N;
+    const long n = vec_len(op);
     const Workspace* pws = c->ws.W ? &c->ws : nullptr;
     // The solve runs on the library's own stream, ordered after the caller's stream at
     // entry and before it at every exit (a stream of its own can carry the L2
@@ -655,7 +655,7 @@ extern "C" die_status gmres_solve(dieop_t op, defl_t defl, const gmres_opts* o, 
 // Gram-Schmidt passes of one system and the FFT passes of another share the GPU.
 static die_status solve_batch_impl(dieop_s* op, defl_s* defl, const gmres_opts* o, int nrhs, const void* b_,
                                    void* x_, gmres_report* reps, void* stream) {
-    const long n = 2L * op->N;
+    const long n = vec_len(op);
     for (int k = 0; k < nrhs; k++) {
         SolverCache* c = reinterpret_cast<SolverCache*>(op->batch[k]);
         const die_status s = ensure_cache(&c, op, o->restart, hist_cap_of(o), true);

@@ -33,7 +33,14 @@ __global__ void contrast_kernel(const double2* __restrict__ eps, long N, double2
 // (Section 2) on the same grid, in both diagonal planes: G11 = G22 = k^2 h^2 (i/4) H0(k r)
 // off the diagonal, and k^2 times the integral of g over the equal-area disc on it,
 // (i pi / 2) k a H1(k a) - 1; G12 = 0, so the two planes never mix.
-__global__ void green_planes_kernel(int n1, int n2, int M1, int M2, double h, double k, int tm,
+//
+// Three planes (mag != 0, DIE_TE_MAG): also the couplings of the magnetic field, from
+// Section 3's compact kernels with eps_b = mu_b = 1, omega = k, d/dx_l g = -(i k/4) H1 theta_l:
+//   plane 3: G13 = G31 = i k d2 g h^2 =  (k^2 h^2 / 4) H1(k r) theta2
+//   plane 4: G23 = G32 = -i k d1 g h^2 = -(k^2 h^2 / 4) H1(k r) theta1
+//   plane 5: G33 = k^2 h^2 (i/4) H0(k r); at r = 0: G13 = G23 = 0 (odd kernels) and G33 =
+//            (i pi / 2) k a H1(k a) - 1, the disc integral of k^2 g (Section 4's [A33]_nn).
+__global__ void green_planes_kernel(int n1, int n2, int M1, int M2, double h, double k, int tm, int mag,
                                     double2* __restrict__ planes) {
     const long plane = (long)M1 * M2;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < plane; idx += (long)gridDim.x * blockDim.x) {
@@ -81,6 +88,28 @@ __global__ void green_planes_kernel(int n1, int n2, int M1, int M2, double h, do
         planes[idx] = g11;
         planes[plane + idx] = g22;
         planes[2 * plane + idx] = g12;
+        if (mag) {
+            double2 g13 = make_double2(0, 0), g23 = make_double2(0, 0), g33 = make_double2(0, 0);
+            if (abs(p) < n1 && abs(q) < n2) {
+                if (p == 0 && q == 0) {
+                    const double ka = k * h * rsqrt(M_PI);
+                    g33 = make_double2(-1.0 - 0.5 * M_PI * ka * y1(ka), 0.5 * M_PI * ka * j1(ka));
+                } else {
+                    const double d1 = p * h, d2 = q * h;
+                    const double r = sqrt(d1 * d1 + d2 * d2);
+                    const double kr = k * r, c = k * k * h * h;
+                    const double J1 = j1(kr), Y1 = y1(kr);
+                    // (c/4) (J1 + i Y1) theta2 and -(c/4) (J1 + i Y1) theta1
+                    g13 = make_double2(0.25 * c * J1 * d2 / r, 0.25 * c * Y1 * d2 / r);
+                    g23 = make_double2(-0.25 * c * J1 * d1 / r, -0.25 * c * Y1 * d1 / r);
+                    // c (i/4) (J0 + i Y0)
+                    g33 = make_double2(-0.25 * c * y0(kr), 0.25 * c * j0(kr));
+                }
+            }
+            planes[3 * plane + idx] = g13;
+            planes[4 * plane + idx] = g23;
+            planes[5 * plane + idx] = g33;
+        }
     }
 }
 
@@ -99,10 +128,11 @@ __global__ void fft_lines_kernel(double2* data, long elem_stride, long line_stri
 }
 
 // gq[plane][k1q][k2q] = spectrum[plane][k2q][k1q] / (M1 M2), k1q <= M1/2, k2q <= M2/2.
-__global__ void quarter_kernel(const double2* __restrict__ spec, int M1, int M2, int Q1, int Q2, double scale,
-                               double2* __restrict__ gq_d, float2* __restrict__ gq_f) {
+__global__ void quarter_kernel(const double2* __restrict__ spec, int nplanes, int M1, int M2, int Q1, int Q2,
+                               double scale, double2* __restrict__ gq_d, float2* __restrict__ gq_f) {
     const long q = (long)Q1 * Q2, plane = (long)M1 * M2;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < 3 * q; idx += (long)gridDim.x * blockDim.x) {
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < nplanes * q;
+         idx += (long)gridDim.x * blockDim.x) {
         const int pl = (int)(idx / q);
         const long rem = idx - pl * q;
         const int k1q = (int)(rem / Q2), k2q = (int)(rem % Q2);
@@ -131,15 +161,35 @@ static die_status fft_lines(double2* data, long elem_stride, long line_stride, i
 die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st) {
     const int M1 = op->M1, M2 = op->M2;
     const long plane = (long)M1 * M2;
+    const int nplanes = green_plane_count(op);
     green_planes_kernel<<<1216, 256, 0, st>>>(op->n1, op->n2, M1, M2, op->h, op->k, op->pol == DIE_TM ? 1 : 0,
-                                               scratch);
+                                               op->planes == 3 ? 1 : 0, scratch);
     DIE_LAUNCH_CHECK();
-    for (int p = 0; p < 3; p++) {
+    for (int p = 0; p < nplanes; p++) {
         double2* base = scratch + p * plane;
         DIE_TRY(fft_lines(base, 1, M1, M2, op->f1, op->tw1_d, st));       // rows: along x1
         DIE_TRY(fft_lines(base, M1, 1, M1, op->f2, op->tw2_d, st));       // columns: along x2
     }
-    quarter_kernel<<<1216, 256, 0, st>>>(scratch, M1, M2, op->Q1, op->Q2, 1.0 / ((double)M1 * M2), op->gq_d, op->gq_f);
+    quarter_kernel<<<1216, 256, 0, st>>>(scratch, nplanes, M1, M2, op->Q1, op->Q2, 1.0 / ((double)M1 * M2), op->gq_d,
+                                         op->gq_f);
+    DIE_LAUNCH_CHECK();
+    return DIE_OK;
+}
+
+// chi_m = mu_r - 1 (Eq. (2.13), mu_b = 1); flags non-finite values.
+__global__ void magnetic_contrast_kernel(const double2* __restrict__ mu, long N, double2* chim_d, float2* chim_f,
+                                         int* flag) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const double2 m = mu[i];
+        if (!isfinite(m.x) || !isfinite(m.y)) { atomicOr(flag, 1); continue; }
+        chim_d[i] = make_double2(m.x - 1.0, m.y);
+        chim_f[i] = make_float2((float)(m.x - 1.0), (float)m.y);
+    }
+}
+
+die_status compute_magnetic_contrast(const dieop_s* op, const double2* mu_dev, double2* chim_d, float2* chim_f,
+                                     int* flag, cudaStream_t st) {
+    magnetic_contrast_kernel<<<608, 256, 0, st>>>(mu_dev, op->N, chim_d, chim_f, flag);
     DIE_LAUNCH_CHECK();
     return DIE_OK;
 }

@@ -12,8 +12,10 @@ OpDev<double> view_d(const dieop_s* op) {
     v.tw1 = op->tw1_d; v.tw2 = op->tw2_d; v.gq = op->gq_d;
     v.twx1 = op->tw1_d + op->M1; v.twx2 = op->tw2_d + op->M2;
     v.tr = 0;
-    v.xs = 2L * op->n1 * op->n2;
-    v.ws = 2L * op->M1 * op->n2;
+    v.chim = op->chim_d;
+    v.planes = op->planes;
+    v.xs = (long)op->planes * op->n1 * op->n2;
+    v.ws = (long)op->planes * op->M1 * op->n2;
     return v;
 }
 OpDev<float> view_f(const dieop_s* op) {
@@ -23,8 +25,10 @@ OpDev<float> view_f(const dieop_s* op) {
     v.tw1 = op->tw1_f; v.tw2 = op->tw2_f; v.gq = op->gq_f;
     v.twx1 = op->tw1_f + op->M1; v.twx2 = op->tw2_f + op->M2;
     v.tr = op->tile_rows_c64;
-    v.xs = 2L * op->n1 * op->n2;
-    v.ws = 2L * op->M1 * op->n2;
+    v.chim = op->chim_f;
+    v.planes = op->planes;
+    v.xs = (long)op->planes * op->n1 * op->n2;
+    v.ws = (long)op->planes * op->M1 * op->n2;
     return v;
 }
 

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(512) k1_rows_fwd(OpDev<T> op, const IO* __rest
         C x[EPT];
         if (active) {
             const IO* urow = u + c * N + (long)i2 * op.n1;
-            const C* crow = chi + (long)i2 * op.n1;
+            const C* crow = (c == 2 ? op.chim : chi) + (long)i2 * op.n1;   // H3 plane: chi_m
 #pragma unroll
             for (int e = 0; e < EPT; e++) {
                 const int idx = reg_index<EPT>(e, R, L, t, G);
@@ -164,6 +164,95 @@ __global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__
             else { gd = g[comp * plane + k2q]; go = g[2 * plane + k2q]; }
             if (neg) { go.x = -go.x; go.y = -go.y; }
             x[e] = comp == 0 ? cadd(cmul(gd, a), cmul(go, b)) : cadd(cmul(go, a), cmul(gd, b));
+        }
+    }
+    __syncthreads();
+    Ns = 1;
+#pragma unroll
+    for (int s = 0; s < nsi; s++) {
+        const int R = LS ? ki.radix[s] : op.i2.radix[s];
+        if (s > 0) {
+            load_any<C, EPT>(R, buf, x, L, t, G);
+            __syncthreads();
+        }
+        compute_any<C, EPT, true>(R, x, L, Ns, t, G, op.tw2);
+        if (s < nsi - 1) {
+            store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                if (idx < op.n2) col[idx] = x[e];
+            }
+        }
+        Ns *= R;
+    }
+}
+
+// The column pass of the three-plane operator (DIE_TE_MAG): threads [0, G), [G, 2G) and
+// [2G, 3G) transform E1, E2 and H3; the 3 x 3 Green multiply reads the six quarter
+// spectra from global memory (planes 0..5: G11, G22, G12, G13, G23, G33).  A spectrum
+// at a mirrored frequency is the stored one times the kernel's parity: G12 (odd in x1 and
+// x2) flips when exactly one of k1, k2 is mirrored, G13 (odd in x2) when k2 is, G23 (odd
+// in x1) when k1 is.
+template <typename T, int EPT, int LS>
+__global__ void __launch_bounds__(768) k2_cols3(OpDev<T> op, C_t<T>* __restrict__ W, const int* __restrict__ skip) {
+    using C = C_t<T>;
+    pdl_wait();
+    if (block_flag(skip)) return;
+    W += blockIdx.y * op.ws;            // right-hand side of a batched product
+    constexpr FftPlan kf = pow2_plan(LS ? LS : 16, false), ki = pow2_plan(LS ? LS : 16, true);
+    const int nsf = LS ? kf.ns : op.f2.ns, nsi = LS ? ki.ns : op.i2.ns;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = LS ? LS : op.M2, G = L / EPT, Lp = padded_len(L);
+    C* bufs = reinterpret_cast<C*>(smem_raw);           // three planes of Lp
+    const int comp = threadIdx.x / G;
+    const int t = threadIdx.x - comp * G;
+    C* buf = bufs + comp * Lp;
+    const int k1 = blockIdx.x;
+    C* col = W + ((long)comp * op.M1 + k1) * op.n2;
+    const int h1 = op.M1 >> 1, h2 = L >> 1;
+    const int Q2 = h2 + 1;
+    const int k1q = k1 <= h1 ? k1 : op.M1 - k1;
+    const bool neg1 = k1 > h1;
+    const long plane = (long)op.Q1 * Q2;
+    const C* g = op.gq + (long)k1q * Q2;
+    C x[EPT];
+    int Ns = 1;
+#pragma unroll
+    for (int s = 0; s < nsf; s++) {
+        const int R = LS ? kf.radix[s] : op.f2.radix[s];
+        if (s == 0) {
+#pragma unroll
+            for (int e = 0; e < EPT; e++) {
+                const int idx = reg_index<EPT>(e, R, L, t, G);
+                x[e] = idx < op.n2 ? col[idx] : czero<C>();
+            }
+        } else {
+            load_any<C, EPT>(R, buf, x, L, t, G);
+            __syncthreads();
+        }
+        compute_any<C, EPT, false>(R, x, L, Ns, t, G, op.tw2);
+        store_any<C, EPT>(R, buf, x, L, Ns, t, G);
+        __syncthreads();
+        Ns *= R;
+    }
+    {   // 3 x 3 Green-spectrum multiply at frequencies (k1, k2)
+        const int R = LS ? ki.radix[0] : op.i2.radix[0];
+#pragma unroll
+        for (int e = 0; e < EPT; e++) {
+            const int k2 = reg_index<EPT>(e, R, L, t, G);
+            const int k2q = k2 <= h2 ? k2 : L - k2;
+            const bool neg2 = k2 > h2;
+            const C a = bufs[pidx(k2)], b = bufs[Lp + pidx(k2)], c = bufs[2 * Lp + pidx(k2)];
+            C g12 = g[2 * plane + k2q], g13 = g[3 * plane + k2q], g23 = g[4 * plane + k2q];
+            if (neg1 != neg2) { g12.x = -g12.x; g12.y = -g12.y; }
+            if (neg2) { g13.x = -g13.x; g13.y = -g13.y; }
+            if (neg1) { g23.x = -g23.x; g23.y = -g23.y; }
+            if (comp == 0) x[e] = cadd(cadd(cmul(g[k2q], a), cmul(g12, b)), cmul(g13, c));
+            else if (comp == 1) x[e] = cadd(cadd(cmul(g12, a), cmul(g[plane + k2q], b)), cmul(g23, c));
+            else x[e] = cadd(cadd(cmul(g13, a), cmul(g23, b)), cmul(g[5 * plane + k2q], c));
         }
     }
     __syncthreads();
@@ -294,7 +383,7 @@ __global__ void __launch_bounds__(512) k3k1_rows(OpDev<T> op, C_t<T>* __restrict
         const int R = iv.radix[iv.ns - 1];      // == f.radix[0]: inverse plan is the reversed forward plan
         if (active) {
             const long off = c * N + (long)i2 * op.n1;
-            const C* crow = chir + (long)i2 * op.n1;
+            const C* crow = (c == 2 ? op.chim : chir) + (long)i2 * op.n1;  // the regulariser keeps chi_m
 #pragma unroll
             for (int e = 0; e < EPT; e++) {
                 const int idx = reg_index<EPT>(e, R, L, t, G);
@@ -774,12 +863,16 @@ inline Launch rows_launch(const OpDev<T>& v) {
     const int G = v.M1 / v.f1.ept;
     int TR = tile_rows<C>();
     while (TR > 1 && TR * G > kRowsMaxThreads) TR /= 2;
-    return Launch{dim3((v.n2 + TR - 1) / TR, 2), dim3(TR * G), (size_t)TR * tile_stride(v.M1) * sizeof(C)};
+    return Launch{dim3((v.n2 + TR - 1) / TR, v.planes), dim3(TR * G), (size_t)TR * tile_stride(v.M1) * sizeof(C)};
 }
 
 template <typename T>
 inline Launch cols_launch(const OpDev<T>& v, int* stage_g) {
     using C = C_t<T>;
+    if (v.planes == 3) {    // three components per column, spectra read from global memory
+        *stage_g = 0;
+        return Launch{dim3(v.M1), dim3(3 * (v.M2 / v.f2.ept)), (size_t)3 * padded_len(v.M2) * sizeof(C)};
+    }
     const size_t base = (size_t)2 * padded_len(v.M2) * sizeof(C);
     const size_t staged = base + (size_t)3 * v.Q2 * sizeof(C);
     *stage_g = staged <= kStageGreenMaxSmem ? 1 : 0;
@@ -813,11 +906,12 @@ inline void launch_kernel(K kernel, std::atomic<bool>& attr_set, const Launch& l
     }
 
 // Grids on the fast path: n = L / 2 with L = 2^a in [256, 4096] (per direction).
+// (Two-plane operators only: the three-plane one runs on the runtime-plan kernels.)
 template <typename T> inline bool fast_rows(const OpDev<T>& v) {
-    return 2 * v.n1 == v.M1 && v.M1 >= 256 && v.M1 <= 4096 && (v.M1 & (v.M1 - 1)) == 0;
+    return v.planes == 2 && 2 * v.n1 == v.M1 && v.M1 >= 256 && v.M1 <= 4096 && (v.M1 & (v.M1 - 1)) == 0;
 }
 template <typename T> inline bool fast_cols(const OpDev<T>& v) {
-    return 2 * v.n2 == v.M2 && v.M2 >= 256 && v.M2 <= 4096 && (v.M2 & (v.M2 - 1)) == 0;
+    return v.planes == 2 && 2 * v.n2 == v.M2 && v.M2 >= 256 && v.M2 <= 4096 && (v.M2 & (v.M2 - 1)) == 0;
 }
 template <typename C, int L, int TR> inline Launch rows_launch_fast(int n2) {
     return Launch{dim3((n2 + TR - 1) / TR, 2), dim3(TR * (L / 16)), (size_t)TR * tile_stride_c<L>() * sizeof(C)};
@@ -893,6 +987,12 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
     int sg = 0;
     Launch l = cols_launch(v, &sg);
     l.grid.y = nb;
+    if (v.planes == 3) {
+        static std::atomic<bool> a16{false}, a12{false};
+        if (v.f2.ept == 16) DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 16, 0>, a16, l, st, v, W, skip));
+        else DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 12, 0>, a12, l, st, v, W, skip));
+        return;
+    }
     if (fast_cols(v)) {
         if constexpr (sizeof(C_t<T>) == 8) {     // complex64: both components per thread
             const Launch l2{l.grid, dim3(v.M2 / 16), l.smem};

@@ -16,10 +16,13 @@ struct OpDev {
     const C* tw2;                 // exp(-2 pi i m / M2)
     const C* twx1;                // stage tables of the compile-time plans along x1 (2 M1)
     const C* twx2;                // the same along x2 (2 M2)
-    const C* gq;                  // quarter spectra of G11, G22, G12: [plane][k1q][k2q], pre-scaled
-    long xs;                      // batched products: elements per field vector (2 n1 n2)
-    long ws;                      // batched products: elements per set of row spectra (2 M1 n2)
+    const C* gq;                  // quarter spectra of G11, G22, G12 (and, with three planes, G13,
+                                  // G23, G33): [plane][k1q][k2q], pre-scaled
+    const C* chim;                // magnetic contrast chi_m (three planes; null otherwise)
+    long xs;                      // batched products: elements per field vector (planes n1 n2)
+    long ws;                      // batched products: elements per set of row spectra (planes M1 n2)
     int tr;                       // tile height of the fast row passes (0: default)
+    int planes;                   // field planes: 2 (E1, E2), or 3 (E1, E2, H3) for DIE_TE_MAG
 };
 
 constexpr int kRowsMaxThreads = 512;    // threads per block of the row passes
@@ -54,10 +57,13 @@ struct dieop_s {
     die::FftPlan f1{}, i1{}, f2{}, i2{};
     double2 *tw1_d = nullptr, *tw2_d = nullptr;   // 3 M entries: natural table, then the
     float2 *tw1_f = nullptr, *tw2_f = nullptr;    // forward and inverse stage tables
-    double2* gq_d = nullptr;       // 3 * Q1 * Q2
+    int planes = 2;                // field planes: 3 for DIE_TE_MAG (E1, E2, H3)
+    double2* gq_d = nullptr;       // (planes == 3 ? 6 : 3) * Q1 * Q2
     float2* gq_f = nullptr;
     double2 *chi_d = nullptr, *chir_d = nullptr;   // chi = eps_r - 1, chi' = 1/eps_r - 1
     float2 *chi_f = nullptr, *chir_f = nullptr;
+    double2* chim_d = nullptr;     // chi_m = mu_r - 1 (DIE_TE_MAG only)
+    float2* chim_f = nullptr;
     die::Workspace ws;             // FP64-sized; the complex64 path uses the first half
     die::Workspace wsb;            // batched products: grown to the largest batch seen
     int wsb_cap = 0;
@@ -70,6 +76,11 @@ struct dieop_s {
 
 namespace die {
 uint64_t next_handle_id();   // process-wide unique identities of operator and deflation handles
+
+// Quarter spectra kept by an operator: G11, G22, G12, and G13, G23, G33 with three planes.
+inline int green_plane_count(const dieop_s* op) { return op->planes == 3 ? 6 : 3; }
+// Complex entries of one field vector.
+inline long vec_len(const dieop_s* op) { return (long)op->planes * op->N; }
 
 OpDev<double> view_d(const dieop_s* op);
 OpDev<float> view_f(const dieop_s* op);

@@ -31,6 +31,7 @@ class DieError(RuntimeError):
 
 DIE_TE = 0
 DIE_TM = 1
+DIE_TE_MAG = 2          # (E1, E2, H3) with magnetic contrast: three planes
 
 
 class Desc(ct.Structure):
@@ -71,6 +72,7 @@ EXPORTS = {
     "dieop_create": (ct.c_int, [ct.POINTER(Desc), ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "dieop_info": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_longlong)]),
     "dieop_set_permittivity": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "dieop_set_permeability": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
     "dieop_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]),
     "dieop_set_tile_rows": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "dieop_tile_rows": (ct.c_int, [ct.c_void_p]),
@@ -217,10 +219,12 @@ class KernelTimer:
 
 
 class Operator:
-    """The discretised TE operator A = I - G X on an n1 x n2 grid (a dieop_t handle)."""
+    """The discretised TE operator A = I - G X on an n1 x n2 grid (a dieop_t handle).
+    pol = DIE_TE_MAG: the (E1, E2, H3) system with magnetic contrast mu_r (field vectors
+    of shape (3, n2, n1))."""
 
     def __init__(self, eps_r, h: float, k_b: float = 2 * math.pi, prec: int = DIE_FP64,
-                 M1: int = 0, M2: int = 0, stream=None, pol: int = DIE_TE):
+                 M1: int = 0, M2: int = 0, stream=None, pol: int = DIE_TE, mu_r=None):
         import numpy as np
         import torch
         eps = eps_r
@@ -244,6 +248,9 @@ class Operator:
         _check(_lib().dieop_info(self._h, info), "dieop_info")
         self.M1, self.M2 = int(info[2]), int(info[3])
         self.N = n1 * n2
+        self.planes = 3 if pol == DIE_TE_MAG else 2
+        if mu_r is not None:
+            self.set_permeability(mu_r, stream)
 
     @property
     def handle(self):
@@ -283,6 +290,22 @@ class Operator:
     def tile_rows(self) -> int:
         return _lib().dieop_tile_rows(self._h)
 
+    def set_permeability(self, mu_r, stream=None):
+        """The relative permeability map of a DIE_TE_MAG operator (chi_m = mu_r - 1)."""
+        import numpy as np
+        import torch
+        if isinstance(mu_r, torch.Tensor) and mu_r.is_cuda:
+            m = mu_r.to(torch.complex128).contiguous()
+            if tuple(m.shape) != (self.n2, self.n1):
+                raise ValueError("mu_r must have shape (n2, n1)")
+            _check(_lib().dieop_set_permeability(self._h, _ptr(m), 1, _stream(stream)), "dieop_set_permeability")
+            return
+        m = np.ascontiguousarray(np.asarray(mu_r, dtype=np.complex128))
+        if m.shape != (self.n2, self.n1):
+            raise ValueError("mu_r must have shape (n2, n1)")
+        _check(_lib().dieop_set_permeability(self._h, m.ctypes.data_as(ct.c_void_p), 0, _stream(stream)),
+               "dieop_set_permeability")
+
     def close(self):
         if getattr(self, "_h", None):
             _lib().dieop_destroy(self._h)
@@ -302,8 +325,8 @@ class Operator:
         import torch
         if x.dtype != self._io_dtype():
             raise TypeError(f"expected {self._io_dtype()}, got {x.dtype}")
-        if x.numel() != 2 * self.N:
-            raise ValueError("vector must hold 2 * n1 * n2 complex values")
+        if x.numel() != self.planes * self.N:
+            raise ValueError("vector must hold planes * n1 * n2 complex values")
         return torch.empty_like(x) if y is None else y
 
     def apply(self, x, y=None, stream=None):
@@ -326,9 +349,9 @@ class Operator:
             raise TypeError("x must be a contiguous CUDA tensor")
         if x.dtype != self._io_dtype():
             raise TypeError(f"expected {self._io_dtype()}, got {x.dtype}")
-        if x.dim() < 1 or x.numel() % (2 * self.N) != 0:
+        if x.dim() < 1 or x.numel() % (self.planes * self.N) != 0:
             raise ValueError("x must hold nrhs field vectors of 2 * n1 * n2 complex values")
-        nrhs = x.numel() // (2 * self.N)
+        nrhs = x.numel() // (self.planes * self.N)
         y = torch.empty_like(x) if y is None else y
         _check(_lib().dieop_apply_batch(self._h, nrhs, _ptr(x), _ptr(y), int(bool(regularized)), _stream(stream)),
                "dieop_apply_batch")
@@ -341,9 +364,9 @@ class Operator:
         return y
 
     def plane_wave(self, psi: float, out=None, stream=None):
-        """Incident TE plane wave at angle psi (complex128, shape (2, n2, n1))."""
+        """Incident TE plane wave at angle psi (complex128, shape (planes, n2, n1))."""
         import torch
-        b = torch.empty((2, self.n2, self.n1), dtype=torch.complex128, device="cuda") if out is None else out
+        b = torch.empty((self.planes, self.n2, self.n1), dtype=torch.complex128, device="cuda") if out is None else out
         _check(_lib().dieop_rhs_plane_wave(self._h, float(psi), _ptr(b), _stream(stream)), "dieop_rhs_plane_wave")
         return b
 
@@ -384,7 +407,7 @@ class Operator:
         """Vectors first .. first + count - 1 of the Krylov basis the last gmres_solve on
         this operator left (complex128, shape (count, 2, n2, n1)); see gmres_basis."""
         import torch
-        out = torch.empty((count, 2, self.n2, self.n1), dtype=torch.complex128, device="cuda")
+        out = torch.empty((count, self.planes, self.n2, self.n1), dtype=torch.complex128, device="cuda")
         _check(_lib().gmres_basis(self._h, int(first), int(count), _ptr(out), _stream(stream)), "gmres_basis")
         return out
 
@@ -396,9 +419,9 @@ class Operator:
         import torch
         if B.dtype != torch.complex128 or not B.is_cuda or not B.is_contiguous():
             raise TypeError("solve_batch takes a contiguous complex128 CUDA tensor")
-        if B.numel() % (2 * self.N) != 0:
-            raise ValueError("B must hold nrhs field vectors of 2 * n1 * n2 values")
-        nrhs = B.numel() // (2 * self.N)
+        if B.numel() % (self.planes * self.N) != 0:
+            raise ValueError("B must hold nrhs field vectors of planes * n1 * n2 values")
+        nrhs = B.numel() // (self.planes * self.N)
         use_x0 = X is not None
         if X is None:
             X = torch.empty_like(B)
@@ -474,7 +497,7 @@ def solve_many(ops, bs, deflations=None, xs=None, restart: int = 30, tol: float 
     if len(bs) != count or (deflations is not None and len(deflations) != count):
         raise ValueError("ops, bs and deflations must have the same length")
     for op, b in zip(ops, bs):
-        if b.dtype != torch.complex128 or not b.is_cuda or not b.is_contiguous() or b.numel() != 2 * op.N:
+        if b.dtype != torch.complex128 or not b.is_cuda or not b.is_contiguous() or b.numel() != op.planes * op.N:
             raise TypeError("solve_many takes contiguous complex128 CUDA tensors of 2 * n1 * n2 values")
     use_x0 = xs is not None
     xs = [torch.empty_like(b) for b in bs] if xs is None else list(xs)
