@@ -1239,19 +1239,8 @@ def config5_budget(args, r: int = 40, restart: int = 40):
     return 0
 
 
-def learned_bench(args):
-    """The learned preconditioner end to end (see paper_1104_4263_gb300/learned.py): pairs,
-    training, evaluation; one JSON line."""
-    import torch
-
-    from paper_1104_4263_gb300 import learned
-    torch.cuda.set_device(0)
-    data = learned.make_dataset(args.pairs)
-    net = learned.default_network(128, max_batch=16)
-    err0 = learned.relative_error(net, data)
-    losses, t_train = learned.train(net, data, epochs=args.epochs)
-    err1 = learned.relative_error(net, data)
-    rows = learned.evaluate(net, args.held_out)
+def _learned_summary(rows):
+    """Means, convergence counts and residual geomeans of learned.evaluate's rows."""
     def mean(key, sub):
         v = [r[sub][key] for r in rows]
         return sum(v) / len(v)
@@ -1275,6 +1264,27 @@ def learned_bench(args):
                                                         for r in rows)
     summary["iteration_ratio"] = summary["without_network"]["mean_iters"] / max(summary["with_network"]["mean_iters"], 1)
     summary["time_ratio"] = summary["without_network"]["mean_s"] / max(summary["with_network"]["mean_s"], 1e-9)
+    return summary
+
+
+def learned_bench(args):
+    """The learned preconditioner end to end (see paper_1104_4263_gb300/learned.py): pairs,
+    training, evaluation; one JSON line."""
+    import torch
+
+    from paper_1104_4263_gb300 import learned
+    torch.cuda.set_device(0)
+    data = learned.make_dataset(args.pairs)
+    net = learned.default_network(128, max_batch=16)
+    err0 = learned.relative_error(net, data)
+    losses, t_train = learned.train(net, data, epochs=args.epochs)
+    err1 = learned.relative_error(net, data)
+    rows = learned.evaluate(net, args.held_out)
+    summary = _learned_summary(rows)
+    # the same network on held-out fields of the same generator with Re eps_r in [1, 16]
+    # (no negative permittivity), where the method without it converges
+    rows_pos = learned.evaluate(net, args.held_out, re_lo=1.0)
+    summary_pos = _learned_summary(rows_pos)
     print(json.dumps({"learned": {
         "grid": 128, "network": {"layers": 4, "modes": 16, "width": 32, "hidden": 128, "params": net.n_params,
                                  "arithmetic": "BF16 tcgen05 GEMMs, FP32 accumulation"},
@@ -1283,6 +1293,7 @@ def learned_bench(args):
         "training": {"epochs": len(losses), "loss_per_epoch": losses, "seconds": t_train,
                      "rel_error_before": err0, "rel_error_after": err1},
         "evaluation": summary, "rows": rows,
+        "evaluation_positive_eps": summary_pos, "rows_positive_eps": rows_pos,
         "tol": 1e-6, "note": ("FGMRES(30) with the network as x0 and right preconditioner for up to 600 steps, "
                               "then the method without it; the network's x0 alone followed by that method; and "
                               "the method alone: regularised + deflated (r = 8) FP32-inner GMRES(100), all to 1e-6 "

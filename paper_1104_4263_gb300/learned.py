@@ -126,8 +126,9 @@ def relative_error(net, data: Dataset, batch: int = 16) -> float:
 
 
 def evaluate(net, count: int, n: int = 128, tol: float = 1e-6, restart: int = 30, base_restart: int = 100,
-             r_defl: int = 8, max_iters: int = 8000, flex_iters: int = 600, first: int = HELD_OUT_BASE):
-    """On `count` held-out fields (plane-wave right-hand sides):
+             r_defl: int = 8, max_iters: int = 8000, flex_iters: int = 600, first: int = HELD_OUT_BASE,
+             re_lo: float = -4.0):
+    """On `count` held-out fields (plane-wave right-hand sides; Re eps_r in [re_lo, 16]):
       * without the network: regularised, deflated (r_defl), FP32-inner GMRES(base_restart)
         from x0 = 0 (the method of Sections 4-5; restart 30 stagnates on these fields);
       * with it: flexible GMRES(restart) with the network as initial guess and right
@@ -137,10 +138,10 @@ def evaluate(net, count: int, n: int = 128, tol: float = 1e-6, restart: int = 30
     deflation build, which is reported apart."""
     import torch
     rows = []
-    p0 = W.config4_field(first, n)
+    p0 = W.config4_field(first, n, re_lo=re_lo)
     op = die.Operator(p0.eps_r, p0.h)
     for i in range(count):
-        p = W.config4_field(first + i, n)
+        p = W.config4_field(first + i, n, re_lo=re_lo)
         op.set_permittivity(p.eps_r)
         b = op.plane_wave(p.psi[0])
         torch.cuda.synchronize()

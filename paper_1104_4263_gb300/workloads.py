@@ -184,17 +184,17 @@ def config3(count: int = 64, sizes=BATCH_SIZES, h: float = 1.0 / 60.0, n_angles:
 
 
 def config4_field(index: int, n: int = 128, h: float = 1.0 / 60.0, corr: float = 0.3,
-                  min_abs: float = 0.25) -> Problem:
+                  min_abs: float = 0.25, re_lo: float = -4.0) -> Problem:
     """Learned-preconditioner workload: a seeded Gaussian random permittivity field over the
-    whole n x n grid, Re eps_r = -4 + 20 Phi(g1) in [-4, 16], Im eps_r = Phi(g2) in [0, 1]
-    (g1, g2 independent unit-variance fields of correlation length `corr`), values with
-    |eps_r| < min_abs pushed out to |eps_r| = min_abs (the existence condition eps != 0),
-    and a random incidence angle.  index selects the seed (training and held-out sets use
-    disjoint ranges)."""
+    whole n x n grid, Re eps_r = re_lo + (16 - re_lo) Phi(g1) in [re_lo, 16] (re_lo = -4 by
+    default), Im eps_r = Phi(g2) in [0, 1] (g1, g2 independent unit-variance fields of
+    correlation length `corr`), values with |eps_r| < min_abs pushed out to |eps_r| = min_abs
+    (the existence condition eps != 0), and a random incidence angle.  index selects the
+    seed (training and held-out sets use disjoint ranges)."""
     rng = rng_for(4, index)
     g1 = _gaussian_field(rng, n, h, corr)
     g2 = _gaussian_field(rng, n, h, corr)
-    eps = (-4.0 + 20.0 * _normal_cdf(g1)) + 1j * _normal_cdf(g2)
+    eps = (re_lo + (16.0 - re_lo) * _normal_cdf(g1)) + 1j * _normal_cdf(g2)
     a = np.abs(eps)
     small = a < min_abs
     eps[small] = np.where(a[small] > 0, eps[small] / np.where(a[small] > 0, a[small], 1.0) * min_abs, min_abs)
