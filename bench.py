@@ -57,6 +57,11 @@ L2_NOTE = "working set > L2 (Krylov basis 31 x 8.4 MB, deflation basis 20 x 4.2 
 # 2N = 524288, from one capture of the committed profile driver (bench.py
 # --profile-driver; the kernel is unchanged since).  Its traffic grows with the vectors
 # read, so it is scaled to the bench's average launch by the algorithmic bytes.
+# DRAM bytes of the five passes of one complex64 regularised product at 512^2 (reads; no
+# DRAM writes were counted during the passes: the row spectra stay in L2)
+NCU_PRODUCT = {"dram_bytes": (6.315520 + 14.774016 + 14.725632 + 14.769408 + 12.608512) * 1e6, "n": 524288,
+               "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:\"k1_fast|k2_fast2|"
+                         "k3k1_fast|k3_fast\" -c 5 on bench.py --profile-driver (its first complex64 product)"}
 NCU_DOTS = {"dram_bytes": 175.365632e6 + 0.137216e6, "nv": 13, "n": 524288,
             "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:proj3 -s 10 -c 3 on "
                       "bench.py --profile-driver (the 13-vector launch; groups of eight vectors)"}
@@ -508,7 +513,9 @@ def main():
     if isinstance(out.get("matvec"), dict) and "c64" in out["matvec"]:
         mv = out["matvec"]["c64"]
         out["roofline_matvec"] = {"bound": "hbm", "achieved": mv["GBps"], "peak": hbm_peak, "unit": "GB/s",
-                                  "frac": mv["GBps"] / hbm_peak, "traffic": None,
+                                  "frac": mv["GBps"] / hbm_peak,
+                                  "traffic": NCU_PRODUCT["dram_bytes"] if 2 * p.N == NCU_PRODUCT["n"] else None,
+                                  "traffic_source": NCU_PRODUCT["source"],
                                   "kernel": "complex64 regularised product (5 passes, one call)",
                                   "algorithmic_bytes_per_launch": mv["algorithmic_bytes"],
                                   "us_per_product": mv["us_per_product"],
