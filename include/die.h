@@ -69,7 +69,7 @@ typedef enum die_precision {
  * second plane stays zero through every product, solve and deflation; the products cost
  * what a TE product costs.
  * DIE_TE_MAG: the full TE system with electric and magnetic contrast, unknowns
- * (E1, E2, H3) of Eq. (2.12) in three planes, A = I - G X, X = diag(chi_e, chi_e, chi_m),
+ * (E1, E2, H3) of Eq. (2.15) in three planes, A = I - G X, X = diag(chi_e, chi_e, chi_m),
  * chi_e = eps_r - 1, chi_m = mu_r - 1 (mu_r from dieop_set_permeability; 1 until then).
  * Besides the electric block of Eqs. (4.3)-(4.5), G has the couplings of Section 3's
  * compact kernels K13, K23, K31, K32, K33 (eps_b = mu_b = 1, omega = k_b):
@@ -119,7 +119,7 @@ die_status dieop_create(const dieop_desc* desc, const void* eps_r, int eps_on_de
  * DIE_EINVAL, DIE_ESINGULAR, DIE_ENOMEM, DIE_ECUDA. */
 die_status dieop_set_permittivity(dieop_t op, const void* eps_r, int eps_on_device, void* stream);
 
-/* Sets the relative permeability map of a DIE_TE_MAG operator: chi_m = mu_r - 1 (Eq. (2.13)).
+/* Sets the relative permeability map of a DIE_TE_MAG operator: chi_m = mu_r - 1 (Section 2's magnetic contrast).
  * mu_r: n1*n2 interleaved complex128, host (mu_on_device = 0) or device.  DIE_EINVAL for
  * another polarisation, DIE_ENAN for a non-finite value (the operator keeps its previous
  * map).  The operator gets a new identity, as for dieop_set_permittivity.  Synchronises

@@ -4,7 +4,7 @@
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Normalised units as in the rest of the oracle: eps_b = mu_b = 1 and omega = k_b, so that
-omega eps_b = omega mu_b = k_b.  The TE integro-differential equation of Eq. (2.12) reads
+omega eps_b = omega mu_b = k_b.  The TE integro-differential equation of Eq. (2.15) reads
 u_in = u - D [g*(chi_e E1), g*(chi_e E2), g*(chi_m H3)] with the differential matrix D of its
 TE line and g = (i/4) H0^(1)(k_b |x|) (Eq. (2.14)).  With d/dx_l g = -(i k/4) H1(k r) theta_l,
 midpoint collocation gives A = I - G X, X = diag(chi_e, chi_e, chi_m), where besides the

@@ -195,7 +195,10 @@ die_status dieop_autotune(dieop_t op, int force, void* stream, int* tile_rows, d
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const int saved = op->tile_rows_c64;
     die_status s = DIE_OK;
-    if (cudaMalloc((void**)&x, bytes) != cudaSuccess || cudaMalloc((void**)&y, bytes) != cudaSuccess) s = DIE_ENOMEM;
+    if (cudaMalloc((void**)&x, bytes) != cudaSuccess || cudaMalloc((void**)&y, bytes) != cudaSuccess) {
+        cudaGetLastError();      // not left for a later launch check to report
+        s = DIE_ENOMEM;
+    }
     if (s == DIE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) s = DIE_ECUDA;
     if (s == DIE_OK && cudaMemsetAsync(x, 0x3c, bytes, st) != cudaSuccess) s = DIE_ECUDA;   // 0x3c3c3c3c ~ 0.0115
     const int heights[4] = {1, 2, 4, 8};

@@ -176,7 +176,7 @@ die_status build_green_spectrum(dieop_s* op, double2* scratch, cudaStream_t st) 
     return DIE_OK;
 }
 
-// chi_m = mu_r - 1 (Eq. (2.13), mu_b = 1); flags non-finite values.
+// chi_m = mu_r - 1 (Section 2's magnetic contrast, mu_b = 1); flags non-finite values.
 __global__ void magnetic_contrast_kernel(const double2* __restrict__ mu, long N, double2* chim_d, float2* chim_f,
                                          int* flag) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
