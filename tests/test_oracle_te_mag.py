@@ -106,3 +106,16 @@ def test_magnetic_pin_catches_a_sign_error(monkeypatch):
     monkeypatch.setattr(te_mag, "coupling", flipped)
     bad = cylinder_error(24, 1.0, 4.0)
     assert bad > 3 * good and bad > 0.3, (good, bad)
+
+
+def test_reciprocity_of_the_discrete_kernel():
+    """Exchanging source and observation cells (x_n - x_m -> x_m - x_n) keeps the even
+    kernels G11, G12, G22, G33 and flips the odd couplings G13 = G31, G23 = G32, so the
+    3N matrix satisfies G^T = S G S with S = diag(1, 1, -1) (reciprocity of the (E1, E2, H3)
+    form).  The printed A31 = -A13 would make G symmetric instead, and fails this."""
+    n1, n2, h = 7, 6, 0.08
+    G = te_mag.dense_G(n1, n2, h, K)
+    N = n1 * n2
+    s = np.concatenate([np.ones(2 * N), -np.ones(N)])
+    assert np.max(np.abs(G.T - s[:, None] * G * s[None, :])) < 1e-13 * np.max(np.abs(G))
+    assert np.max(np.abs(G.T - G)) > 1e-3 * np.max(np.abs(G))
