@@ -96,6 +96,13 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.gmres_solve_many(1, None, None, ct.byref(opts), dummy, dummy, None, None) == 1
     nulls = ct.cast((ct.c_void_p * 1)(None), ct.c_void_p)     # ops[0] == NULL
     assert lib.gmres_solve_many(1, nulls, None, ct.byref(opts), nulls, nulls, None, None) == 1
+    # the magnetic-contrast operator and the tile schedule
+    d = die.Desc(8, 8, 0.1, 0.0, 0, 0, 0, 3)          # no such polarisation
+    assert lib.dieop_create(ct.byref(d), eps.ctypes.data_as(ct.c_void_p), 0, None, ct.byref(out)) == 1
+    assert lib.dieop_set_permeability(None, None, 0, None) == 1
+    assert lib.dieop_set_tile_rows(None, 4) == 1
+    assert lib.dieop_tile_rows(None) == 0
+    assert lib.dieop_autotune(None, 0, None, None, None) == 1
 
 
 def test_solve_many_argument_checks_without_gpu():
