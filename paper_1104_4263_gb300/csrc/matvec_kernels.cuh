@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(512) k2_cols(OpDev<T> op, C_t<T>* __restrict__
 // at a mirrored frequency is the stored one times the kernel's parity: G12 (odd in x1 and
 // x2) flips when exactly one of k1, k2 is mirrored, G13 (odd in x2) when k2 is, G23 (odd
 // in x1) when k1 is.
-template <typename T, int EPT, int LS>
-__global__ void __launch_bounds__(768) k2_cols3(OpDev<T> op, C_t<T>* __restrict__ W, const int* __restrict__ skip) {
+template <typename T, int EPT, int LS, int MAXT>
+__global__ void __launch_bounds__(MAXT) k2_cols3(OpDev<T> op, C_t<T>* __restrict__ W, const int* __restrict__ skip) {
     using C = C_t<T>;
     pdl_wait();
     if (block_flag(skip)) return;
@@ -987,10 +987,16 @@ inline void launch_k2(const OpDev<T>& v, C_t<T>* W, const int* skip, cudaStream_
     int sg = 0;
     Launch l = cols_launch(v, &sg);
     l.grid.y = nb;
-    if (v.planes == 3) {
-        static std::atomic<bool> a16{false}, a12{false};
-        if (v.f2.ept == 16) DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 16, 0>, a16, l, st, v, W, skip));
-        else DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 12, 0>, a12, l, st, v, W, skip));
+    if (v.planes == 3) {   // 3 G threads: at most 384 up to M2 = 2048, 768 beyond (fewer registers)
+        static std::atomic<bool> a16{false}, a12{false}, b16{false}, b12{false};
+        const bool small = l.block.x <= 384;
+        if (v.f2.ept == 16) {
+            if (small) DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 16, 0, 384>, a16, l, st, v, W, skip));
+            else DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 16, 0, 768>, b16, l, st, v, W, skip));
+        } else {
+            if (small) DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 12, 0, 384>, a12, l, st, v, W, skip));
+            else DIE_PROF(PK_COLS, st, launch_kernel(k2_cols3<T, 12, 0, 768>, b12, l, st, v, W, skip));
+        }
         return;
     }
     if (fast_cols(v)) {
